@@ -1,0 +1,166 @@
+/*
+ * lbrr.h - C ABI of the GB300 (sm_103a) recursive-regularized BGK lattice
+ * Boltzmann library, liblbrr.so.
+ *
+ * The method is the regularized collide-and-stream update of Malaspinas,
+ * arXiv:1505.06900, Sec. 3.4 (eq_discr_bgk_reg):
+ *
+ *     f_i(x + xi_i, t + 1) = f0_i + (1 - 1/tau) f1_i,
+ *
+ * where f0 is the equilibrium expanded on the full D2Q9 / D3Q27 Hermite basis
+ * (Sec. 3.2, eq_fzero_d2q9 / eq_fzero_d3q27), f1 the off-equilibrium part
+ * (eq_fone_d2q9 / eq_fone_d3q27) whose coefficients of order n >= 3 follow
+ * from u and a1^(2) = Pi^(1) by the recursion of Sec. 3.1 (eq_rel_a1,
+ * Appendix B without the starred terms), and tau is the shifted relaxation
+ * time tau-bar of Sec. 3.3 (kinematic viscosity nu = (tau - 1/2) / 3).
+ *
+ * Conventions shared by every call:
+ *  - Lattices: D2Q9 (nz must be 1) and D3Q27. Velocity i has components
+ *    (i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1); the opposite velocity is Q-1-i.
+ *  - Fields are structure-of-arrays, x fastest: element (c, z, y, x) of a
+ *    field with C components is at ((c * nz + z) * ny + y) * nx + x.
+ *  - Populations exchanged with the caller are "shifted": df_i = f_i - w_i,
+ *    float32, one array of Q * nx * ny * nz values.
+ *  - Pointers documented as device pointers must point to memory of the
+ *    context's device (cudaMalloc, torch tensors); the caller owns them.
+ *  - All work is ordered on the context's stream (lb_set_stream); calls that
+ *    return values to host memory synchronise that stream.
+ *  - Every call returns LB_OK or an error code; on error the context's state
+ *    is unchanged unless stated otherwise and lb_last_error() explains it.
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef LBRR_H
+#define LBRR_H
+
+#if defined(__GNUC__)
+#define LB_API __attribute__((visibility("default")))
+#else
+#define LB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define LB_OK 0
+#define LB_EINVAL 1    /* bad argument (lattice, sizes, tau <= 1/2, null pointer ...) */
+#define LB_ENOMEM 2    /* a device or host allocation failed */
+#define LB_ECUDA 3     /* a CUDA call or kernel launch failed */
+#define LB_EDIVERGED 4 /* a diagnostic is not finite: the run has blown up */
+
+/* lattices */
+#define LB_D2Q9 9
+#define LB_D3Q27 27
+
+/* storage of the populations in device memory */
+#define LB_STORE_F32 0  /* df_i = f_i - w_i as float32 (4 bytes) */
+#define LB_STORE_F16 1  /* (f_i - w_i) / w_i as IEEE binary16, round to nearest even */
+#define LB_STORE_BF16 2 /* (f_i - w_i) / w_i as bfloat16, round to nearest even */
+
+/* collision models */
+#define LB_COLLIDE_RR 0   /* recursive regularized, Sec. 3.4 (the paper's model) */
+#define LB_COLLIDE_REG2 1 /* order-2 regularized comparator, Sec. 3.6.1 (eq_feq_2) */
+
+/* initialisation modes of lb_init_fields */
+#define LB_INIT_EQ 0        /* f = f0(rho, u) */
+#define LB_INIT_EQ_NEQ_FD 1 /* f = f0 + f1 with a1^(2) = -2 c_s^2 rho tau S, S by periodic
+                               central differences of u (Sec. 3.3, constitutive relation) */
+
+typedef struct lb_ctx lb_ctx;
+
+typedef struct lb_options {
+  int lattice;    /* LB_D2Q9 or LB_D3Q27 */
+  int nx, ny, nz; /* grid size in cells, each >= 1; nz == 1 for D2Q9 */
+  double tau;     /* shifted relaxation time tau-bar > 1/2 (Sec. 3.3) */
+  int periodic;   /* must be 1: every face is periodic */
+  int storage;    /* LB_STORE_* */
+  int collision;  /* LB_COLLIDE_* */
+} lb_options;
+
+/* Create a context holding one device population store of Q*nx*ny*nz values
+ * (AA pattern: one buffer, updated in place) on the current CUDA device. The
+ * populations start at rest (f = w, rho = 1, u = 0). Storage F32, model RR.
+ * Returns LB_EINVAL for a bad lattice, a size < 1, nz != 1 with D2Q9,
+ * tau <= 1/2 or periodic != 1; LB_ENOMEM if the store does not fit.
+ * Sec. 3.2 (q populations per node), Sec. 3.3 (tau). */
+LB_API int lb_create(lb_ctx **out, int lattice, int nx, int ny, int nz, double tau, int periodic);
+
+/* As lb_create, with the storage precision and collision model chosen. */
+LB_API int lb_create_ex(lb_ctx **out, const lb_options *opt);
+
+/* Free the context and its device memory. NULL is accepted. */
+LB_API void lb_destroy(lb_ctx *ctx);
+
+/* Text of the last error on this context; with ctx == NULL, of the last
+ * failed lb_create/lb_create_ex on the calling thread. Never NULL. */
+LB_API const char *lb_last_error(const lb_ctx *ctx);
+
+/* Order all later work of the context on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream). */
+LB_API int lb_set_stream(lb_ctx *ctx, void *stream);
+
+/* Set the populations from macroscopic fields (device pointers): rho [N],
+ * u [D][N], float32. init_mode LB_INIT_EQ or LB_INIT_EQ_NEQ_FD. Resets the
+ * step count. Sec. 3.2 (eq_fzero_*), Sec. 3.1 (eq_rel_a1), Sec. 3.3. */
+LB_API int lb_init_fields(lb_ctx *ctx, const float *rho, const float *u, int init_mode);
+
+/* Advance n >= 0 full collide-and-stream updates (eq_discr_bgk_reg). n == 0 is
+ * a no-op. Asynchronous on the context's stream. */
+LB_API int lb_step(lb_ctx *ctx, int n);
+
+/* Macroscopic fields of the current populations into device buffers:
+ * rho [N], u [D][N], pi1 [3 or 6][N] (xx, xy, yy in 2D; xx, xy, xz, yy, yz, zz
+ * in 3D) with pi1 = a1^(2) = sum xi xi f - rho c_s^2 I - rho u u (Sec. 2,
+ * P^(1) = a1^(2)). Any pointer may be NULL to skip that field. */
+LB_API int lb_moments(lb_ctx *ctx, float *rho, float *u, float *pi1);
+
+/* Global diagnostics in double precision into host memory out[2 + D]:
+ * mass sum rho, momentum sum rho u (D values), kinetic energy
+ * 0.5 sum rho |u|^2. Deterministic (fixed reduction order). Synchronises the
+ * stream. Returns LB_EDIVERGED (out still filled) if a value is not finite.
+ * Uses a device scratch buffer owned by the context. */
+LB_API int lb_diagnostics(lb_ctx *ctx, double *out);
+
+/* Enstrophy 0.5 sum |curl u|^2 with periodic central differences (2D:
+ * omega = d_x u_y - d_y u_x; the enstrophy of Sec. 4.1 summed over cells),
+ * double precision, into host memory *out. Synchronises the stream. */
+LB_API int lb_enstrophy(lb_ctx *ctx, double *out);
+
+/* Copy the current populations, in natural order and shifted form
+ * df_i(x) = f_i(x) - w_i, float32, into the device buffer dst [Q][N]. */
+LB_API int lb_get_populations(lb_ctx *ctx, float *dst);
+
+/* Replace the populations by the shifted float32 values src [Q][N] (device),
+ * rounded to the storage precision. Resets the step count. */
+LB_API int lb_set_populations(lb_ctx *ctx, const float *src);
+
+/* Size in bytes of the raw device store (for lb_get_state / lb_set_state). */
+LB_API long long lb_state_bytes(const lb_ctx *ctx);
+
+/* Copy the raw store (storage precision, AA slot order) and the step count
+ * parity to dst (host or device memory, lb_state_bytes bytes) - a checkpoint.
+ * Synchronises the stream. */
+LB_API int lb_get_state(lb_ctx *ctx, void *dst, int *parity);
+
+/* Restore a checkpoint written by lb_get_state of a context with the same
+ * lattice, size and storage. parity must be 0 or 1. */
+LB_API int lb_set_state(lb_ctx *ctx, const void *src, int parity);
+
+/* End-to-end run through host memory: copy rho_h [N] and u_h [D][N] (host,
+ * float32; pinned memory makes the copies asynchronous) to the device,
+ * initialise with init_mode, advance nsteps, and copy the final rho and u
+ * into rho_out_h / u_out_h (host, may be NULL) and the diagnostics of
+ * lb_diagnostics into diag_h[2 + D] (host, may be NULL). Synchronises. */
+LB_API int lb_run_host(lb_ctx *ctx, const float *rho_h, const float *u_h, int init_mode, int nsteps,
+                       float *rho_out_h, float *u_out_h, double *diag_h);
+
+/* Description of a context into out[8]: lattice, nx, ny, nz, storage,
+ * collision, number of steps taken, bytes moved per cell update. */
+LB_API int lb_info(const lb_ctx *ctx, long long *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBRR_H */

@@ -1,0 +1,216 @@
+"""ctypes binding of liblbrr.so (the C ABI of include/lbrr.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. torch supplies device memory and the stream. The library must have
+been built (``paper_1505_06900_gb300.build.build()``); ``load()`` raises if it
+is missing rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "liblbrr.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED = 0, 1, 2, 3, 4
+D2Q9, D3Q27 = 9, 27
+STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
+COLLIDE_RR, COLLIDE_REG2 = 0, 1
+INIT_EQ, INIT_EQ_NEQ_FD = 0, 1
+
+# every entry point of include/lbrr.h with its ctypes signature
+_vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+SIGNATURES = {
+    "lb_create": (_i, [ctypes.POINTER(_vp), _i, _i, _i, _i, _d, _i]),
+    "lb_create_ex": (_i, [ctypes.POINTER(_vp), _vp]),
+    "lb_destroy": (None, [_vp]),
+    "lb_last_error": (ctypes.c_char_p, [_vp]),
+    "lb_set_stream": (_i, [_vp, _vp]),
+    "lb_init_fields": (_i, [_vp, _vp, _vp, _i]),
+    "lb_step": (_i, [_vp, _i]),
+    "lb_moments": (_i, [_vp, _vp, _vp, _vp]),
+    "lb_diagnostics": (_i, [_vp, _vp]),
+    "lb_enstrophy": (_i, [_vp, _vp]),
+    "lb_get_populations": (_i, [_vp, _vp]),
+    "lb_set_populations": (_i, [_vp, _vp]),
+    "lb_state_bytes": (_ll, [_vp]),
+    "lb_get_state": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "lb_set_state": (_i, [_vp, _vp, _i]),
+    "lb_run_host": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
+    "lb_info": (_i, [_vp, ctypes.POINTER(_ll)]),
+}
+
+
+class LBOptions(ctypes.Structure):
+    _fields_ = [("lattice", _i), ("nx", _i), ("ny", _i), ("nz", _i), ("tau", _d),
+                ("periodic", _i), ("storage", _i), ("collision", _i)]
+
+
+class LBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"lbrr error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbrr.so (once). Raises if the library has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} not found: build it with paper_1505_06900_gb300.build")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def dims_of(lattice: int) -> tuple[int, int]:
+    return (2, 9) if lattice == D2Q9 else (3, 27)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a contiguous torch tensor or numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous(), "tensors passed to lbrr must be contiguous"
+    return t.data_ptr()
+
+
+class Solver:
+    """One lattice Boltzmann context (device population store) of liblbrr.so."""
+
+    def __init__(self, lattice: int, shape, tau: float, storage: int = STORE_F32,
+                 collision: int = COLLIDE_RR, stream=None):
+        import torch
+        self._lib = load()
+        self.lattice = lattice
+        self.d, self.q = dims_of(lattice)
+        self.nx, self.ny, self.nz = (list(shape) + [1])[:3] if len(shape) == 2 else shape
+        self.n = self.nx * self.ny * self.nz
+        self.tau = float(tau)
+        opt = LBOptions(lattice, self.nx, self.ny, self.nz, self.tau, 1, storage, collision)
+        h = ctypes.c_void_p()
+        rc = self._lib.lb_create_ex(ctypes.byref(h), ctypes.addressof(opt))
+        if rc != LB_OK:
+            raise LBError(rc, self._lib.lb_last_error(None).decode())
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.set_stream(stream if stream is not None else torch.cuda.current_stream())
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != LB_OK:
+            raise LBError(rc, self._lib.lb_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self._lib.lb_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def _field(self, comps):
+        import torch
+        return torch.empty((comps, self.nz, self.ny, self.nx), device=self.device,
+                           dtype=torch.float32)
+
+    # -- the method -------------------------------------------------------
+    def init_fields(self, rho, u, mode: int = INIT_EQ_NEQ_FD):
+        """rho [nz,ny,nx] and u [D,nz,ny,nx] float32 CUDA tensors."""
+        rho = rho.contiguous()
+        u = u.contiguous()
+        assert rho.numel() == self.n and u.numel() == self.d * self.n
+        assert rho.is_cuda and u.is_cuda and rho.dtype == u.dtype
+        self._check(self._lib.lb_init_fields(self._h, _ptr(rho), _ptr(u), int(mode)))
+        self._keep = (rho, u)  # keep alive until the stream has consumed them
+
+    def step(self, n: int = 1):
+        self._check(self._lib.lb_step(self._h, int(n)))
+
+    def moments(self):
+        """(rho [nz,ny,nx], u [D,...], pi1 [3|6,...]) as CUDA tensors."""
+        rho, u, p = self._field(1), self._field(self.d), self._field(3 if self.d == 2 else 6)
+        self._check(self._lib.lb_moments(self._h, _ptr(rho), _ptr(u), _ptr(p)))
+        return rho[0], u, p
+
+    def diagnostics(self) -> np.ndarray:
+        out = np.zeros(2 + self.d)
+        rc = self._lib.lb_diagnostics(self._h, out.ctypes.data)
+        if rc == LB_EDIVERGED:
+            raise LBError(rc, self._lib.lb_last_error(self._h).decode())
+        self._check(rc)
+        return out
+
+    def enstrophy(self) -> float:
+        out = np.zeros(1)
+        self._check(self._lib.lb_enstrophy(self._h, out.ctypes.data))
+        return float(out[0])
+
+    def populations(self):
+        """Shifted populations df [Q, nz, ny, nx] (float32, natural order)."""
+        out = self._field(self.q)
+        self._check(self._lib.lb_get_populations(self._h, _ptr(out)))
+        return out
+
+    def set_populations(self, df):
+        df = df.contiguous()
+        assert df.numel() == self.q * self.n and df.is_cuda
+        self._check(self._lib.lb_set_populations(self._h, _ptr(df)))
+        self._keep = (df,)
+
+    def state_bytes(self) -> int:
+        return int(self._lib.lb_state_bytes(self._h))
+
+    def get_state(self, dst):
+        par = ctypes.c_int()
+        self._check(self._lib.lb_get_state(self._h, _ptr(dst), ctypes.byref(par)))
+        return par.value
+
+    def set_state(self, src, parity: int):
+        self._check(self._lib.lb_set_state(self._h, _ptr(src), int(parity)))
+
+    def run_host(self, rho_h: np.ndarray, u_h: np.ndarray, nsteps: int,
+                 mode: int = INIT_EQ_NEQ_FD, rho_out=None, u_out=None, diag_out=None):
+        """End-to-end run from host arrays (numpy or pinned CPU tensors)."""
+        self._check(self._lib.lb_run_host(self._h, _ptr(rho_h), _ptr(u_h), int(mode), int(nsteps),
+                                          _ptr(rho_out), _ptr(u_out), _ptr(diag_out)))
+
+    def info(self) -> dict:
+        out = (ctypes.c_longlong * 8)()
+        self._check(self._lib.lb_info(self._h, out))
+        keys = ["lattice", "nx", "ny", "nz", "storage", "collision", "steps", "bytes_per_update"]
+        return dict(zip(keys, list(out)))

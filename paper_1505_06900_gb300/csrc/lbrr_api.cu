@@ -1,0 +1,352 @@
+// C ABI of liblbrr.so (declared in include/lbrr.h): context management,
+// argument validation, error reporting and the ordering of kernel launches on
+// the context's stream. No arithmetic of the method lives here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbrr.h"
+#include "lbrr_launch.h"
+
+struct lb_ctx {
+  int lattice = 0, d = 0, q = 0;
+  lbrr::Grid g{};
+  double tau = 0.0;
+  int storage = LB_STORE_F32, collision = LB_COLLIDE_RR;
+  int parity = 0;          // AA parity: 0 natural order, 1 after an odd number of updates
+  long long steps = 0;     // updates since the last (re)initialisation
+  int device = 0;
+  size_t elem = 4;         // bytes per stored population
+  void *f = nullptr;       // population store, q * n elements
+  double *partials = nullptr;  // reduction scratch, kRedBlocks * kRedValues doubles
+  double *dout = nullptr;      // reduction result, kRedValues doubles
+  float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_create_err[512] = "no error";
+
+int fail(lb_ctx *c, int code, const char *fmt, ...) {
+  char *buf = c ? c->err : g_create_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(lb_ctx *c, cudaError_t e, const char *what) {
+  return fail(c, LB_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define LB_CHECK_CTX(c)                                         \
+  do {                                                          \
+    if (!(c)) return fail(nullptr, LB_EINVAL, "null context");  \
+  } while (0)
+
+// Make the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int free_all(lb_ctx *c) {
+  if (c->f) cudaFree(c->f);
+  if (c->partials) cudaFree(c->partials);
+  if (c->dout) cudaFree(c->dout);
+  if (c->fields) cudaFree(c->fields);
+  c->f = nullptr;
+  c->partials = nullptr;
+  c->dout = nullptr;
+  c->fields = nullptr;
+  return 0;
+}
+
+int ensure_fields(lb_ctx *c) {
+  if (c->fields) return LB_OK;
+  cudaError_t e = cudaMalloc(&c->fields, sizeof(float) * (size_t)(1 + c->d) * (size_t)c->g.n);
+  if (e != cudaSuccess) {
+    c->fields = nullptr;
+    cudaGetLastError();
+    return fail(c, LB_ENOMEM, "cannot allocate %lld bytes of field scratch",
+                (long long)(sizeof(float) * (size_t)(1 + c->d) * (size_t)c->g.n));
+  }
+  return LB_OK;
+}
+
+// Deterministic FP64 diagnostics into host out[2 + d].
+int diagnostics(lb_ctx *c, double *out) {
+  cudaError_t e = lbrr::launch_diagnostics(c->q, c->storage, c->f, c->g, c->parity, c->partials,
+                                           c->dout, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics launch");
+  double h[lbrr::kRedValues];
+  e = cudaMemcpyAsync(h, c->dout, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics copy");
+  out[0] = (double)c->g.n + h[0];
+  for (int a = 0; a < c->d; ++a) out[1 + a] = h[1 + a];
+  out[1 + c->d] = h[4];
+  for (int k = 0; k < 2 + c->d; ++k)
+    if (!std::isfinite(out[k])) return fail(c, LB_EDIVERGED, "diagnostic %d is not finite", k);
+  return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lb_create_ex(lb_ctx **out, const lb_options *opt) {
+  if (!out || !opt) return fail(nullptr, LB_EINVAL, "null argument");
+  *out = nullptr;
+  const int lat = opt->lattice;
+  if (lat != LB_D2Q9 && lat != LB_D3Q27) return fail(nullptr, LB_EINVAL, "unknown lattice %d", lat);
+  if (opt->nx < 1 || opt->ny < 1 || opt->nz < 1)
+    return fail(nullptr, LB_EINVAL, "grid sizes must be >= 1 (got %d x %d x %d)", opt->nx, opt->ny,
+                opt->nz);
+  if (lat == LB_D2Q9 && opt->nz != 1) return fail(nullptr, LB_EINVAL, "D2Q9 needs nz == 1");
+  if (opt->ny > 65535 || opt->nz > 65535)
+    return fail(nullptr, LB_EINVAL, "ny and nz must be <= 65535");
+  if (!(opt->tau > 0.5) || !std::isfinite(opt->tau))
+    return fail(nullptr, LB_EINVAL, "tau must be a finite number > 1/2 (got %g)", opt->tau);
+  if (opt->periodic != 1) return fail(nullptr, LB_EINVAL, "only fully periodic grids are supported");
+  if (opt->storage < LB_STORE_F32 || opt->storage > LB_STORE_BF16)
+    return fail(nullptr, LB_EINVAL, "unknown storage %d", opt->storage);
+  if (opt->collision != LB_COLLIDE_RR && opt->collision != LB_COLLIDE_REG2)
+    return fail(nullptr, LB_EINVAL, "unknown collision model %d", opt->collision);
+  const long long n = (long long)opt->nx * opt->ny * opt->nz;
+  if (n > (1LL << 40)) return fail(nullptr, LB_EINVAL, "grid too large");
+
+  lb_ctx *c = new (std::nothrow) lb_ctx;
+  if (!c) return fail(nullptr, LB_ENOMEM, "host allocation failed");
+  c->lattice = lat;
+  c->q = lat;
+  c->d = lat == LB_D2Q9 ? 2 : 3;
+  c->g = lbrr::Grid{opt->nx, opt->ny, opt->nz, n};
+  c->tau = opt->tau;
+  c->storage = opt->storage;
+  c->collision = opt->collision;
+  c->elem = opt->storage == LB_STORE_F32 ? 4 : 2;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  const size_t bytes = c->elem * (size_t)c->q * (size_t)n;
+  e = cudaMalloc(&c->f, bytes);
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->partials, sizeof(double) * lbrr::kRedBlocks * lbrr::kRedValues);
+  if (e == cudaSuccess) e = cudaMalloc(&c->dout, sizeof(double) * lbrr::kRedValues);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return fail(nullptr, LB_ENOMEM, "cannot allocate %zu bytes of population store", bytes);
+  }
+  // rest state: df = 0 in every storage precision
+  e = cudaMemset(c->f, 0, bytes);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return fail(nullptr, LB_ECUDA, "initial clear failed: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return LB_OK;
+}
+
+int lb_create(lb_ctx **out, int lattice, int nx, int ny, int nz, double tau, int periodic) {
+  lb_options o{lattice, nx, ny, nz, tau, periodic, LB_STORE_F32, LB_COLLIDE_RR};
+  return lb_create_ex(out, &o);
+}
+
+void lb_destroy(lb_ctx *c) {
+  if (!c) return;
+  DeviceGuard dg(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+const char *lb_last_error(const lb_ctx *c) { return c ? c->err : g_create_err; }
+
+int lb_set_stream(lb_ctx *c, void *stream) {
+  LB_CHECK_CTX(c);
+  c->stream = static_cast<cudaStream_t>(stream);
+  return LB_OK;
+}
+
+int lb_init_fields(lb_ctx *c, const float *rho, const float *u, int init_mode) {
+  LB_CHECK_CTX(c);
+  if (!rho || !u) return fail(c, LB_EINVAL, "rho and u must be device pointers");
+  if (init_mode != LB_INIT_EQ && init_mode != LB_INIT_EQ_NEQ_FD)
+    return fail(c, LB_EINVAL, "unknown init mode %d", init_mode);
+  DeviceGuard dg(c->device);
+  cudaError_t e = lbrr::launch_init(c->q, c->storage, c->collision, c->f, c->g, rho, u,
+                                    (float)c->tau, init_mode, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init launch");
+  c->parity = 0;
+  c->steps = 0;
+  return LB_OK;
+}
+
+int lb_step(lb_ctx *c, int n) {
+  LB_CHECK_CTX(c);
+  if (n < 0) return fail(c, LB_EINVAL, "negative step count %d", n);
+  DeviceGuard dg(c->device);
+  const float om1 = (float)(1.0 - 1.0 / c->tau);
+  for (int k = 0; k < n; ++k) {
+    cudaError_t e =
+        lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    c->parity ^= 1;
+    ++c->steps;
+  }
+  return LB_OK;
+}
+
+int lb_moments(lb_ctx *c, float *rho, float *u, float *pi1) {
+  LB_CHECK_CTX(c);
+  if (!rho && !u && !pi1) return LB_OK;
+  DeviceGuard dg(c->device);
+  cudaError_t e =
+      lbrr::launch_moments(c->q, c->storage, c->f, c->g, c->parity, rho, u, pi1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "moments launch");
+  return LB_OK;
+}
+
+int lb_diagnostics(lb_ctx *c, double *out) {
+  LB_CHECK_CTX(c);
+  if (!out) return fail(c, LB_EINVAL, "null output");
+  DeviceGuard dg(c->device);
+  return diagnostics(c, out);
+}
+
+int lb_enstrophy(lb_ctx *c, double *out) {
+  LB_CHECK_CTX(c);
+  if (!out) return fail(c, LB_EINVAL, "null output");
+  DeviceGuard dg(c->device);
+  int rc = ensure_fields(c);
+  if (rc != LB_OK) return rc;
+  float *u = c->fields + c->g.n;
+  cudaError_t e = lbrr::launch_moments(c->q, c->storage, c->f, c->g, c->parity, nullptr, u,
+                                       nullptr, c->stream);
+  if (e == cudaSuccess) e = lbrr::launch_enstrophy(c->d, u, c->g, c->partials, c->dout, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->dout, sizeof(double), cudaMemcpyDeviceToHost,
+                                            c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "enstrophy");
+  if (!std::isfinite(*out)) return fail(c, LB_EDIVERGED, "enstrophy is not finite");
+  return LB_OK;
+}
+
+int lb_get_populations(lb_ctx *c, float *dst) {
+  LB_CHECK_CTX(c);
+  if (!dst) return fail(c, LB_EINVAL, "null destination");
+  DeviceGuard dg(c->device);
+  cudaError_t e =
+      lbrr::launch_get_populations(c->q, c->storage, c->f, c->g, c->parity, dst, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_populations launch");
+  return LB_OK;
+}
+
+int lb_set_populations(lb_ctx *c, const float *src) {
+  LB_CHECK_CTX(c);
+  if (!src) return fail(c, LB_EINVAL, "null source");
+  DeviceGuard dg(c->device);
+  cudaError_t e = lbrr::launch_set_populations(c->q, c->storage, c->f, c->g, src, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_populations launch");
+  c->parity = 0;
+  c->steps = 0;
+  return LB_OK;
+}
+
+long long lb_state_bytes(const lb_ctx *c) {
+  return c ? (long long)(c->elem * (size_t)c->q * (size_t)c->g.n) : -1;
+}
+
+int lb_get_state(lb_ctx *c, void *dst, int *parity) {
+  LB_CHECK_CTX(c);
+  if (!dst || !parity) return fail(c, LB_EINVAL, "null argument");
+  DeviceGuard dg(c->device);
+  cudaError_t e = cudaMemcpyAsync(dst, c->f, (size_t)lb_state_bytes(c), cudaMemcpyDefault,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
+  *parity = c->parity;
+  return LB_OK;
+}
+
+int lb_set_state(lb_ctx *c, const void *src, int parity) {
+  LB_CHECK_CTX(c);
+  if (!src) return fail(c, LB_EINVAL, "null source");
+  if (parity != 0 && parity != 1) return fail(c, LB_EINVAL, "parity must be 0 or 1");
+  DeviceGuard dg(c->device);
+  cudaError_t e = cudaMemcpyAsync(c->f, src, (size_t)lb_state_bytes(c), cudaMemcpyDefault,
+                                  c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
+  c->parity = parity;
+  c->steps = parity;
+  return LB_OK;
+}
+
+int lb_run_host(lb_ctx *c, const float *rho_h, const float *u_h, int init_mode, int nsteps,
+                float *rho_out_h, float *u_out_h, double *diag_h) {
+  LB_CHECK_CTX(c);
+  if (!rho_h || !u_h) return fail(c, LB_EINVAL, "rho and u must be host pointers");
+  if (nsteps < 0) return fail(c, LB_EINVAL, "negative step count");
+  if (init_mode != LB_INIT_EQ && init_mode != LB_INIT_EQ_NEQ_FD)
+    return fail(c, LB_EINVAL, "unknown init mode %d", init_mode);
+  DeviceGuard dg(c->device);
+  int rc = ensure_fields(c);
+  if (rc != LB_OK) return rc;
+  const size_t nb = sizeof(float) * (size_t)c->g.n;
+  float *rho_d = c->fields, *u_d = c->fields + c->g.n;
+  cudaError_t e = cudaMemcpyAsync(rho_d, rho_h, nb, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(u_d, u_h, nb * c->d, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "run_host upload");
+  rc = lb_init_fields(c, rho_d, u_d, init_mode);
+  if (rc == LB_OK) rc = lb_step(c, nsteps);
+  if (rc != LB_OK) return rc;
+  if (rho_out_h || u_out_h) {
+    rc = lb_moments(c, rho_d, u_d, nullptr);
+    if (rc != LB_OK) return rc;
+    if (rho_out_h) e = cudaMemcpyAsync(rho_out_h, rho_d, nb, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && u_out_h)
+      e = cudaMemcpyAsync(u_out_h, u_d, nb * c->d, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "run_host download");
+  }
+  if (diag_h) return diagnostics(c, diag_h);
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "run_host");
+  return LB_OK;
+}
+
+int lb_info(const lb_ctx *c, long long *out) {
+  if (!c || !out) return LB_EINVAL;
+  out[0] = c->lattice;
+  out[1] = c->g.nx;
+  out[2] = c->g.ny;
+  out[3] = c->g.nz;
+  out[4] = c->storage;
+  out[5] = c->collision;
+  out[6] = c->steps;
+  out[7] = 2LL * c->q * (long long)c->elem;
+  return LB_OK;
+}
+
+}  // extern "C"

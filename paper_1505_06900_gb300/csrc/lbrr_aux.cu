@@ -1,0 +1,365 @@
+// Initialisation, moment extraction, population copies and the FP64
+// diagnostics reductions of the RR lattice Boltzmann library.
+#include <type_traits>
+
+#include "lbrr_launch.h"
+
+namespace lbrr {
+
+constexpr int kAuxThreads = 128;
+
+// Logical (natural-order, pre-collision) shifted populations of cell (x, y, z)
+// from an AA store of the given parity (see lbrr_step.cu).
+template <int Q, int S>
+__device__ __forceinline__ void load_logical(const typename Storage<S>::T *__restrict__ f,
+                                             const Grid &g, int parity, int x, int y, int z,
+                                             float (&df)[Q]) {
+  constexpr int D = Lattice<Q>::D;
+  const long long n = g.n;
+  if (parity == 0) {
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) df[i] = Storage<S>::template load<D>(f + i * n + cell, i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int xs = wrap_add(x, -vel(i, 0), g.nx), ys = wrap_add(y, -vel(i, 1), g.ny);
+      const int zs = D == 3 ? wrap_add(z, -vel(i, 2), g.nz) : 0;
+      const long long src = ((long long)zs * g.ny + ys) * g.nx + xs;
+      df[i] = Storage<S>::template load<D>(f + (Q - 1 - i) * n + src, i);
+    }
+  }
+}
+
+__device__ __forceinline__ void cell_coords(long long cell, const Grid &g, int &x, int &y,
+                                            int &z) {
+  x = (int)(cell % g.nx);
+  const long long r = cell / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
+}
+
+// ------------------------------------------------------------------ init --
+// f = f0(rho, u) [+ f1 with a1^(2) = -2 cs2 rho tau S]: the constitutive
+// relation of Sec. 3.3 in lattice units, with tau the scheme's tau-bar; the
+// higher orders of f1 follow from the recursion inside synth (om1 = 1).
+template <int Q, int S, int MODEL>
+__global__ void __launch_bounds__(kAuxThreads)
+    init_kernel(typename Storage<S>::T *__restrict__ f, const Grid g,
+                const float *__restrict__ rho, const float *__restrict__ u, const float tau,
+                const int mode) {
+  using L = Lattice<Q>;
+  constexpr int D = L::D;
+  const long long cell = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  const long long n = g.n;
+  Macro m;
+  m.rho = rho[cell];
+  m.drho = m.rho - 1.0f;
+  m.ux = u[cell];
+  m.uy = u[n + cell];
+  m.uz = D == 3 ? u[2 * n + cell] : 0.0f;
+  m.pxx = m.pxy = m.pxz = m.pyy = m.pyz = m.pzz = 0.0f;
+  if (mode == 1) {
+    // du[b][a] = d u_b / d x_a by periodic central differences
+    float du[3][3] = {};
+    const int p[3] = {x, y, z};
+    const int dims[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int pp[3] = {p[0], p[1], p[2]}, pm[3] = {p[0], p[1], p[2]};
+      pp[a] = wrap_add(p[a], 1, dims[a]);
+      pm[a] = wrap_add(p[a], -1, dims[a]);
+      const long long cp = ((long long)pp[2] * g.ny + pp[1]) * g.nx + pp[0];
+      const long long cm = ((long long)pm[2] * g.ny + pm[1]) * g.nx + pm[0];
+#pragma unroll
+      for (int b = 0; b < D; ++b) du[b][a] = 0.5f * (u[b * n + cp] - u[b * n + cm]);
+    }
+    const float k = -2.0f * kCs2 * m.rho * tau;
+    m.pxx = k * du[0][0];
+    m.pyy = k * du[1][1];
+    m.pxy = k * 0.5f * (du[0][1] + du[1][0]);
+    if (D == 3) {
+      m.pzz = k * du[2][2];
+      m.pxz = k * 0.5f * (du[0][2] + du[2][0]);
+      m.pyz = k * 0.5f * (du[1][2] + du[2][1]);
+    }
+  }
+  float df[Q];
+  L::template synth<MODEL>(m, 1.0f, df);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) Storage<S>::template store<D>(f + i * n + cell, i, df[i]);
+}
+
+// ----------------------------------------------------------- populations --
+template <int Q, int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    get_populations_kernel(const typename Storage<S>::T *__restrict__ f, const Grid g,
+                           const int parity, float *__restrict__ dst) {
+  const long long cell = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  float df[Q];
+  load_logical<Q, S>(f, g, parity, x, y, z, df);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) dst[i * g.n + cell] = df[i];
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    set_populations_kernel(typename Storage<S>::T *__restrict__ f, const Grid g,
+                           const float *__restrict__ src) {
+  constexpr int D = Lattice<Q>::D;
+  const long long cell = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (cell >= g.n) return;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    Storage<S>::template store<D>(f + i * g.n + cell, i, src[i * g.n + cell]);
+}
+
+// --------------------------------------------------------------- moments --
+template <int Q, int S>
+__global__ void __launch_bounds__(kAuxThreads)
+    moments_kernel(const typename Storage<S>::T *__restrict__ f, const Grid g, const int parity,
+                   float *__restrict__ rho, float *__restrict__ u, float *__restrict__ pi1) {
+  constexpr int D = Lattice<Q>::D;
+  const long long cell = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  float df[Q];
+  load_logical<Q, S>(f, g, parity, x, y, z, df);
+  const Macro m = Lattice<Q>::moments(df);
+  const long long n = g.n;
+  if (rho) rho[cell] = m.rho;
+  if (u) {
+    u[cell] = m.ux;
+    u[n + cell] = m.uy;
+    if (D == 3) u[2 * n + cell] = m.uz;
+  }
+  if (pi1) {
+    if (D == 2) {
+      pi1[cell] = m.pxx;
+      pi1[n + cell] = m.pxy;
+      pi1[2 * n + cell] = m.pyy;
+    } else {
+      pi1[cell] = m.pxx;
+      pi1[n + cell] = m.pxy;
+      pi1[2 * n + cell] = m.pxz;
+      pi1[3 * n + cell] = m.pyy;
+      pi1[4 * n + cell] = m.pyz;
+      pi1[5 * n + cell] = m.pzz;
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions --
+// Block sum of NV doubles per thread: warp shuffles, then one value per warp
+// in shared memory, then the first warp. The order is fixed, so results are
+// reproducible run to run.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
+  __shared__ double sm[kRedThreads / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[warp][k] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < kRedThreads / 32 ? sm[lane][k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) out[k] = s;
+    }
+  }
+}
+
+template <int Q, int S>
+__global__ void __launch_bounds__(kRedThreads)
+    diag_partial_kernel(const typename Storage<S>::T *__restrict__ f, const Grid g,
+                        const int parity, double *__restrict__ partials) {
+  double acc[kRedValues] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const long long stride = (long long)gridDim.x * kRedThreads;
+  for (long long cell = (long long)blockIdx.x * kRedThreads + threadIdx.x; cell < g.n;
+       cell += stride) {
+    int x, y, z;
+    cell_coords(cell, g, x, y, z);
+    float df[Q];
+    load_logical<Q, S>(f, g, parity, x, y, z, df);
+    const Macro m = Lattice<Q>::moments(df);
+    const double r = m.rho, ux = m.ux, uy = m.uy, uz = m.uz;
+    acc[0] += (double)m.drho;
+    acc[1] += r * ux;
+    acc[2] += r * uy;
+    acc[3] += r * uz;
+    acc[4] += 0.5 * r * (ux * ux + uy * uy + uz * uz);
+  }
+  block_sum<kRedValues>(acc, partials + (long long)blockIdx.x * kRedValues);
+}
+
+// Sums nblocks rows of nv partials in a fixed order into out[nv].
+__global__ void __launch_bounds__(kRedThreads)
+    finalize_kernel(const double *__restrict__ partials, int nblocks, int nv,
+                    double *__restrict__ out) {
+  for (int k = 0; k < nv; ++k) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < nblocks; b += kRedThreads) v[0] += partials[(long long)b * nv + k];
+    __shared__ double res[1];
+    block_sum<1>(v, res);
+    __syncthreads();
+    if (threadIdx.x == 0) out[k] = res[0];
+    __syncthreads();
+  }
+}
+
+// 0.5 |curl u|^2 per cell with periodic central differences.
+template <int D>
+__global__ void __launch_bounds__(kRedThreads)
+    enstrophy_partial_kernel(const float *__restrict__ u, const Grid g,
+                             double *__restrict__ partials) {
+  double acc[1] = {0.0};
+  const long long n = g.n;
+  const long long stride = (long long)gridDim.x * kRedThreads;
+  for (long long cell = (long long)blockIdx.x * kRedThreads + threadIdx.x; cell < n;
+       cell += stride) {
+    int x, y, z;
+    cell_coords(cell, g, x, y, z);
+    auto at = [&](int comp, int xx, int yy, int zz) -> double {
+      return (double)u[comp * n + ((long long)zz * g.ny + yy) * g.nx + xx];
+    };
+    const int xp = wrap_add(x, 1, g.nx), xm = wrap_add(x, -1, g.nx);
+    const int yp = wrap_add(y, 1, g.ny), ym = wrap_add(y, -1, g.ny);
+    // d_a u_b = (u_b(x + e_a) - u_b(x - e_a)) / 2
+    const double dxuy = 0.5 * (at(1, xp, y, z) - at(1, xm, y, z));
+    const double dyux = 0.5 * (at(0, x, yp, z) - at(0, x, ym, z));
+    const double wz = dxuy - dyux;
+    double wx = 0.0, wy = 0.0;
+    if (D == 3) {
+      const int zp = wrap_add(z, 1, g.nz), zm = wrap_add(z, -1, g.nz);
+      const double dyuz = 0.5 * (at(2, x, yp, z) - at(2, x, ym, z));
+      const double dzuy = 0.5 * (at(1, x, y, zp) - at(1, x, y, zm));
+      const double dzux = 0.5 * (at(0, x, y, zp) - at(0, x, y, zm));
+      const double dxuz = 0.5 * (at(2, xp, y, z) - at(2, xm, y, z));
+      wx = dyuz - dzuy;
+      wy = dzux - dxuz;
+    }
+    acc[0] += 0.5 * (wx * wx + wy * wy + wz * wz);
+  }
+  block_sum<1>(acc, partials + blockIdx.x);
+}
+
+// --------------------------------------------------------------- launchers --
+static dim3 cells_grid(long long n) { return dim3((unsigned)((n + kAuxThreads - 1) / kAuxThreads)); }
+
+static int red_blocks(long long n) {
+  long long b = (n + kRedThreads - 1) / kRedThreads;
+  return (int)(b < kRedBlocks ? b : kRedBlocks);
+}
+
+// Calls fn(integral_constant<Q>, integral_constant<S>) for the runtime
+// lattice size q and storage code.
+template <class F>
+static void dispatch_qs(int q, int storage, F &&fn) {
+  using std::integral_constant;
+  if (q == 9) {
+    if (storage == 0) fn(integral_constant<int, 9>{}, integral_constant<int, 0>{});
+    else if (storage == 1) fn(integral_constant<int, 9>{}, integral_constant<int, 1>{});
+    else fn(integral_constant<int, 9>{}, integral_constant<int, 2>{});
+  } else {
+    if (storage == 0) fn(integral_constant<int, 27>{}, integral_constant<int, 0>{});
+    else if (storage == 1) fn(integral_constant<int, 27>{}, integral_constant<int, 1>{});
+    else fn(integral_constant<int, 27>{}, integral_constant<int, 2>{});
+  }
+}
+
+cudaError_t launch_init(int q, int storage, int model, void *f, const Grid &g, const float *rho,
+                        const float *u, float tau, int mode, cudaStream_t st) {
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    if (model == 0)
+      init_kernel<Q_, S_, 0><<<cells_grid(g.n), kAuxThreads, 0, st>>>(static_cast<T *>(f), g,
+                                                                        rho, u, tau, mode);
+    else
+      init_kernel<Q_, S_, 1><<<cells_grid(g.n), kAuxThreads, 0, st>>>(static_cast<T *>(f), g,
+                                                                        rho, u, tau, mode);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(int q, int storage, const void *f, const Grid &g, int parity,
+                                   float *dst, cudaStream_t st) {
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    get_populations_kernel<Q_, S_><<<cells_grid(g.n), kAuxThreads, 0, st>>>(
+        static_cast<const T *>(f), g, parity, dst);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(int q, int storage, void *f, const Grid &g, const float *src,
+                                   cudaStream_t st) {
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    set_populations_kernel<Q_, S_><<<cells_grid(g.n), kAuxThreads, 0, st>>>(static_cast<T *>(f),
+                                                                            g, src);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int q, int storage, const void *f, const Grid &g, int parity,
+                           float *rho, float *u, float *pi1, cudaStream_t st) {
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    moments_kernel<Q_, S_><<<cells_grid(g.n), kAuxThreads, 0, st>>>(static_cast<const T *>(f), g,
+                                                                     parity, rho, u, pi1);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g, int parity,
+                               double *partials, double *out, cudaStream_t st) {
+  const int nb = red_blocks(g.n);
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    diag_partial_kernel<Q_, S_><<<nb, kRedThreads, 0, st>>>(static_cast<const T *>(f), g, parity,
+                                                            partials);
+  });
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<<<1, kRedThreads, 0, st>>>(partials, nb, kRedValues, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
+                             cudaStream_t st) {
+  const int nb = red_blocks(g.n);
+  if (d == 2)
+    enstrophy_partial_kernel<2><<<nb, kRedThreads, 0, st>>>(u, g, partials);
+  else
+    enstrophy_partial_kernel<3><<<nb, kRedThreads, 0, st>>>(u, g, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<<<1, kRedThreads, 0, st>>>(partials, nb, 1, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbrr

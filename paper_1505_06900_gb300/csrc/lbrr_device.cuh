@@ -1,0 +1,394 @@
+// Device-side building blocks of the recursive-regularized (RR) BGK step
+// (arXiv:1505.06900): storage conversion, moments, and the reconstruction
+// f_post = f0 + (1 - 1/tau) f1 of Sec. 3.4 on the D2Q9 / D3Q27 Hermite bases.
+//
+// The kernel does not evaluate the paper's Hermite sums term by term. Both
+// lattices are tensor products of the D1Q3 rule, so their Hermite bases are
+// tensor products of the 1-D set {1, xi, xi^2 - c_s^2}. On that basis:
+//  * the equilibrium coefficient of x^a y^b z^c (a, b, c in {0, 1, 2}) is
+//    rho ux^a uy^b uz^c (Sec. 2, a0^(n) = a0^(n-1) u of Sec. 3.1);
+//  * the off-equilibrium coefficients given by the recursion eq_rel_a1
+//    (Appendix B, starred terms dropped) equal, in closed form, the sum over
+//    index pairs of a1^(2) times the velocity components of the other indices,
+//    i.e. C1 = 1/2 sum_ab Pi_ab d^2/du_a du_b (ux^a uy^b uz^c);
+//  * the population of velocity (xi_x, xi_y, xi_z) is the separable synthesis
+//    f = (T (x) T (x) T) C with the 1-D map
+//      T(c0, c1, c2)(xi) = w_xi (c0 + 3 xi c1 + 9/2 (xi^2 - 1/3) c2).
+// The coefficient tensor of f0 + (1 - 1/tau) f1 is a sum of three rank-one
+// terms along x (u_x powers, their second and first u_x derivatives), so the
+// synthesis runs x first on those terms and then applies T along y and z.
+// All values carried are shifted by the rest state (df = f - w), which keeps
+// float32 round-off relative to the deviations rather than to w.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbrr {
+
+constexpr float kCs2 = 1.0f / 3.0f;
+
+// D1Q3 weight of xi = k - 1 (k = 0, 1, 2)
+__host__ __device__ constexpr float w1(int k) { return k == 1 ? 2.0f / 3.0f : 1.0f / 6.0f; }
+// T(0, 0, 1) at xi = k - 1: the second u-derivative factor (1/2, -1, 1/2)
+__host__ __device__ constexpr float hh1(int k) { return k == 1 ? -1.0f : 0.5f; }
+
+// weight of velocity i of a D-dimensional tensor-product lattice
+template <int D>
+__host__ __device__ constexpr float weight(int i) {
+  return D == 2 ? w1(i % 3) * w1((i / 3) % 3) : w1(i % 3) * w1((i / 3) % 3) * w1(i / 9);
+}
+// 1 / w_i (exact in float32: products of 6 and 3/2)
+template <int D>
+__host__ __device__ constexpr float inv_weight(int i) {
+  return D == 2 ? (1.0f / w1(i % 3)) * (1.0f / w1((i / 3) % 3))
+                : (1.0f / w1(i % 3)) * (1.0f / w1((i / 3) % 3)) * (1.0f / w1(i / 9));
+}
+
+// ---------------------------------------------------------------- storage --
+// LB_STORE_F32: df_i as float. LB_STORE_F16 / LB_STORE_BF16: df_i / w_i in
+// 16 bits, round to nearest even.
+template <int S>
+struct Storage;
+
+template <>
+struct Storage<0> {
+  using T = float;
+  template <int D>
+  __device__ __forceinline__ static float load(const T *p, int i) {
+    return *p;
+  }
+  template <int D>
+  __device__ __forceinline__ static void store(T *p, int i, float v) {
+    *p = v;
+  }
+};
+
+template <>
+struct Storage<1> {
+  using T = __half;
+  template <int D>
+  __device__ __forceinline__ static float load(const T *p, int i) {
+    return __half2float(*p) * weight<D>(i);
+  }
+  template <int D>
+  __device__ __forceinline__ static void store(T *p, int i, float v) {
+    *p = __float2half_rn(v * inv_weight<D>(i));
+  }
+};
+
+template <>
+struct Storage<2> {
+  using T = __nv_bfloat16;
+  template <int D>
+  __device__ __forceinline__ static float load(const T *p, int i) {
+    return __bfloat162float(*p) * weight<D>(i);
+  }
+  template <int D>
+  __device__ __forceinline__ static void store(T *p, int i, float v) {
+    *p = __float2bfloat16_rn(v * inv_weight<D>(i));
+  }
+};
+
+// ---------------------------------------------------------------- moments --
+// rho, u and a1^(2) = Pi1 = sum xi xi f - rho cs2 I - rho u u (Sec. 2) from
+// shifted populations: rho - 1 = sum df, rho u = sum xi df, and
+// sum xi xi f = sum xi xi df + cs2 I (the rest state's second moment).
+struct Macro {
+  float drho, rho, ux, uy, uz;
+  float pxx, pxy, pxz, pyy, pyz, pzz;
+};
+
+// Moments of a D2Q9 cell, separable sums over x then y.
+__device__ __forceinline__ Macro moments_d2q9(const float (&f)[9]) {
+  float s0[3], s1[3], s2[3];  // per y-line: sum, first and second x-moment
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    const float a = f[3 * l], b = f[3 * l + 1], c = f[3 * l + 2];
+    s2[l] = a + c;
+    s0[l] = s2[l] + b;
+    s1[l] = c - a;
+  }
+  Macro m;
+  const float m00 = s0[0] + s0[1] + s0[2];
+  const float m01 = s0[2] - s0[0];
+  const float m02 = s0[2] + s0[0];
+  const float m10 = s1[0] + s1[1] + s1[2];
+  const float m11 = s1[2] - s1[0];
+  const float m20 = s2[0] + s2[1] + s2[2];
+  m.drho = m00;
+  m.rho = 1.0f + m00;
+  const float inv = 1.0f / m.rho;
+  m.ux = m10 * inv;
+  m.uy = m01 * inv;
+  m.uz = 0.0f;
+  m.pxx = m20 - kCs2 * m00 - m10 * m.ux;
+  m.pxy = m11 - m10 * m.uy;
+  m.pyy = m02 - kCs2 * m00 - m01 * m.uy;
+  m.pxz = m.pyz = m.pzz = 0.0f;
+  return m;
+}
+
+// Moments of a D3Q27 cell, separable sums over x, then y, then z.
+__device__ __forceinline__ Macro moments_d3q27(const float (&f)[27]) {
+  float x0[9], x1[9], x2[9];
+#pragma unroll
+  for (int l = 0; l < 9; ++l) {
+    const float a = f[3 * l], b = f[3 * l + 1], c = f[3 * l + 2];
+    x2[l] = a + c;
+    x0[l] = x2[l] + b;
+    x1[l] = c - a;
+  }
+  // y-pass per z-plane k: moments (x-power p, y-power q) with p + q <= 2
+  float y00[3], y01[3], y02[3], y10[3], y11[3], y20[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int l = 3 * k;
+    y02[k] = x0[l] + x0[l + 2];
+    y00[k] = y02[k] + x0[l + 1];
+    y01[k] = x0[l + 2] - x0[l];
+    y10[k] = x1[l] + x1[l + 1] + x1[l + 2];
+    y11[k] = x1[l + 2] - x1[l];
+    y20[k] = x2[l] + x2[l + 1] + x2[l + 2];
+  }
+  const float m000 = y00[0] + y00[1] + y00[2];
+  const float m001 = y00[2] - y00[0];
+  const float m002 = y00[2] + y00[0];
+  const float m010 = y01[0] + y01[1] + y01[2];
+  const float m011 = y01[2] - y01[0];
+  const float m020 = y02[0] + y02[1] + y02[2];
+  const float m100 = y10[0] + y10[1] + y10[2];
+  const float m101 = y10[2] - y10[0];
+  const float m110 = y11[0] + y11[1] + y11[2];
+  const float m200 = y20[0] + y20[1] + y20[2];
+  Macro m;
+  m.drho = m000;
+  m.rho = 1.0f + m000;
+  const float inv = 1.0f / m.rho;
+  m.ux = m100 * inv;
+  m.uy = m010 * inv;
+  m.uz = m001 * inv;
+  m.pxx = m200 - kCs2 * m000 - m100 * m.ux;
+  m.pyy = m020 - kCs2 * m000 - m010 * m.uy;
+  m.pzz = m002 - kCs2 * m000 - m001 * m.uz;
+  m.pxy = m110 - m100 * m.uy;
+  m.pxz = m101 - m100 * m.uz;
+  m.pyz = m011 - m010 * m.uz;
+  return m;
+}
+
+// ------------------------------------------------------------- synthesis --
+// 1-D synthesis T of coefficients (c0, c1, c2) at xi = -1, 0, +1.
+__device__ __forceinline__ void synth1(float c0, float c1, float c2, float &om, float &oz,
+                                       float &op) {
+  const float q = fmaf(c0, kCs2, c2);
+  oz = c0 - q;
+  op = 0.5f * (q + c1);
+  om = 0.5f * (q - c1);
+}
+
+// Per-axis factors at xi = -1, 0, +1 for velocity component u:
+//  dg = g(xi, u) - w_xi, with g the 1-D equilibrium T(1, u, u^2);
+//  dd = T(0, 1, 2u)  (first u-derivative of g);  hh = T(0, 0, 1) = (1/2, -1, 1/2).
+struct Axis {
+  float dg[3], dd[3];
+};
+__device__ __forceinline__ Axis axis_factors(float u) {
+  Axis a;
+  const float uu = u * u;
+  a.dg[0] = 0.5f * (uu - u);
+  a.dg[1] = -uu;
+  a.dg[2] = 0.5f * (uu + u);
+  a.dd[0] = u - 0.5f;
+  a.dd[1] = -2.0f * u;
+  a.dd[2] = u + 0.5f;
+  return a;
+}
+
+// Shifted post-collision populations of a D2Q9 cell (RR, Sec. 3.4):
+// df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1 rebuilds f0 + f1).
+__device__ __forceinline__ void synth_rr_d2q9(const Macro &m, float om1, float (&f)[9]) {
+  const Axis ax = axis_factors(m.ux);
+  const float uy = m.uy, uyy = uy * uy;
+  const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pxy = om1 * m.pxy;
+  // y-coefficient vectors of the three x-terms (b = 0, 1, 2):
+  //  Q1 = rho (1, uy, uy^2) + Pi_yy (0, 0, 1)   [paired with g_x]
+  //  Q2 = Pi_xx (1, uy, uy^2)                    [paired with hh]
+  //  Q3 = Pi_xy (0, 1, 2 uy)                     [paired with dd_x]
+  const float q1[3] = {m.rho, m.rho * uy, fmaf(m.rho, uyy, pyy)};
+  const float q2[3] = {pxx, pxx * uy, pxx * uyy};
+  const float q3[3] = {0.0f, pxy, 2.0f * pxy * uy};
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) {
+    const float wx = w1(ix), gx = wx + ax.dg[ix], hx = hh1(ix), dx = ax.dd[ix];
+    // b = 0 carries the shift: g_x rho - w_x = w_x drho + dg_x rho
+    const float r0 = fmaf(hx, q2[0], fmaf(ax.dg[ix], m.rho, wx * m.drho));
+    const float r1 = fmaf(dx, q3[1], fmaf(hx, q2[1], gx * q1[1]));
+    const float r2 = fmaf(dx, q3[2], fmaf(hx, q2[2], gx * q1[2]));
+    float om, oz, op;
+    synth1(r0, r1, r2, om, oz, op);
+    f[ix] = om;
+    f[ix + 3] = oz;
+    f[ix + 6] = op;
+  }
+}
+
+// Shifted post-collision populations of a D3Q27 cell (RR, Sec. 3.4).
+__device__ __forceinline__ void synth_rr_d3q27(const Macro &m, float om1, float (&f)[27]) {
+  const Axis ax = axis_factors(m.ux);
+  const float uy = m.uy, uz = m.uz;
+  const float py[3] = {1.0f, uy, uy * uy}, pz[3] = {1.0f, uz, uz * uz};
+  const float dy[3] = {0.0f, 1.0f, 2.0f * uy}, dz[3] = {0.0f, 1.0f, 2.0f * uz};
+  const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pzz = om1 * m.pzz;
+  const float pxy = om1 * m.pxy, pxz = om1 * m.pxz, pyz = om1 * m.pyz;
+  // (y, z) coefficient matrices of the three x-terms, index [b][c]:
+  //  Q1 = rho py pz + Pi_yy h py' + Pi_zz py h' + Pi_yz dy dz   [with g_x]
+  //  Q2 = Pi_xx py pz                                            [with hh]
+  //  Q3 = Pi_xy dy pz + Pi_xz py dz                              [with dd_x]
+  float q1[3][3], q2[3][3], q3[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float pp = py[b] * pz[c];
+      float v = m.rho * pp;
+      if (b == 2) v = fmaf(pyy, pz[c], v);
+      if (c == 2) v = fmaf(pzz, py[b], v);
+      if (b > 0 && c > 0) v = fmaf(pyz, dy[b] * dz[c], v);
+      q1[b][c] = v;
+      q2[b][c] = pxx * pp;
+      float w = 0.0f;
+      if (b > 0) w = fmaf(pxy, dy[b] * pz[c], w);
+      if (c > 0) w = fmaf(pxz, py[b] * dz[c], w);
+      q3[b][c] = w;
+    }
+  }
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) {
+    const float wx = w1(ix), gx = wx + ax.dg[ix], hx = hh1(ix), dx = ax.dd[ix];
+    float r[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (b == 0 && c == 0) {
+          // shifted entry: g_x rho - w_x = w_x drho + dg_x rho (q3[0][0] = 0)
+          r[0][0] = fmaf(hx, q2[0][0], fmaf(ax.dg[ix], m.rho, wx * m.drho));
+        } else {
+          r[b][c] = fmaf(dx, q3[b][c], fmaf(hx, q2[b][c], gx * q1[b][c]));
+        }
+      }
+    }
+    // synthesis along y for each z-coefficient c, then along z
+    float s[3][3];  // [iy][c]
+#pragma unroll
+    for (int c = 0; c < 3; ++c) synth1(r[0][c], r[1][c], r[2][c], s[0][c], s[1][c], s[2][c]);
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy) {
+      float om, oz, op;
+      synth1(s[iy][0], s[iy][1], s[iy][2], om, oz, op);
+      f[ix + 3 * iy] = om;
+      f[ix + 3 * iy + 9] = oz;
+      f[ix + 3 * iy + 18] = op;
+    }
+  }
+}
+
+// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
+// coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
+__device__ __forceinline__ void synth_reg2_d2q9(const Macro &m, float om1, float (&f)[9]) {
+  float c[3][3] = {};  // [a][b] coefficient of x^a y^b
+  c[0][0] = m.drho;
+  c[1][0] = m.rho * m.ux;
+  c[0][1] = m.rho * m.uy;
+  c[2][0] = fmaf(om1, m.pxx, m.rho * m.ux * m.ux);
+  c[0][2] = fmaf(om1, m.pyy, m.rho * m.uy * m.uy);
+  c[1][1] = fmaf(om1, m.pxy, m.rho * m.ux * m.uy);
+  float s[3][3];  // [ix][b]
+#pragma unroll
+  for (int b = 0; b < 3; ++b) synth1(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) synth1(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
+}
+
+__device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, float (&f)[27]) {
+  float c[3][3][3] = {};  // [a][b][c]
+  c[0][0][0] = m.drho;
+  c[1][0][0] = m.rho * m.ux;
+  c[0][1][0] = m.rho * m.uy;
+  c[0][0][1] = m.rho * m.uz;
+  c[2][0][0] = fmaf(om1, m.pxx, m.rho * m.ux * m.ux);
+  c[0][2][0] = fmaf(om1, m.pyy, m.rho * m.uy * m.uy);
+  c[0][0][2] = fmaf(om1, m.pzz, m.rho * m.uz * m.uz);
+  c[1][1][0] = fmaf(om1, m.pxy, m.rho * m.ux * m.uy);
+  c[1][0][1] = fmaf(om1, m.pxz, m.rho * m.ux * m.uz);
+  c[0][1][1] = fmaf(om1, m.pyz, m.rho * m.uy * m.uz);
+  float sx[3][3][3];  // [ix][b][c]
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      synth1(c[0][b][cc], c[1][b][cc], c[2][b][cc], sx[0][b][cc], sx[1][b][cc], sx[2][b][cc]);
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) {
+    float sy[3][3];  // [iy][c]
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      synth1(sx[ix][0][cc], sx[ix][1][cc], sx[ix][2][cc], sy[0][cc], sy[1][cc], sy[2][cc]);
+#pragma unroll
+    for (int iy = 0; iy < 3; ++iy)
+      synth1(sy[iy][0], sy[iy][1], sy[iy][2], f[ix + 3 * iy], f[ix + 3 * iy + 9],
+             f[ix + 3 * iy + 18]);
+  }
+}
+
+template <int Q>
+struct Lattice;
+template <>
+struct Lattice<9> {
+  static constexpr int D = 2;
+  __device__ __forceinline__ static Macro moments(const float (&f)[9]) { return moments_d2q9(f); }
+  template <int MODEL>
+  __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[9]) {
+    if (MODEL == 0)
+      synth_rr_d2q9(m, om1, f);
+    else
+      synth_reg2_d2q9(m, om1, f);
+  }
+};
+template <>
+struct Lattice<27> {
+  static constexpr int D = 3;
+  __device__ __forceinline__ static Macro moments(const float (&f)[27]) {
+    return moments_d3q27(f);
+  }
+  template <int MODEL>
+  __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[27]) {
+    if (MODEL == 0)
+      synth_rr_d3q27(m, om1, f);
+    else
+      synth_reg2_d3q27(m, om1, f);
+  }
+};
+
+// velocity component a of direction i
+__host__ __device__ constexpr int vel(int i, int a) {
+  return a == 0 ? i % 3 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1);
+}
+
+// Grid geometry passed by value to every kernel.
+struct Grid {
+  int nx, ny, nz;
+  long long n;  // nx * ny * nz (cells per population slot)
+};
+
+// Periodic neighbour coordinate c + d, d in {-1, 0, 1}.
+__device__ __forceinline__ int wrap_add(int c, int d, int n) {
+  int r = c + d;
+  r = (r < 0) ? r + n : r;
+  return (r >= n) ? r - n : r;
+}
+
+}  // namespace lbrr

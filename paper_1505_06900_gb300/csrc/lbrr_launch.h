@@ -1,0 +1,46 @@
+// Host-side launchers of the CUDA kernels (internal to liblbrr.so).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbrr_device.cuh"
+
+namespace lbrr {
+
+// Number of per-block partial sums of the deterministic reductions.
+constexpr int kRedBlocks = 1216;   // 152 SMs x 8
+constexpr int kRedThreads = 256;
+constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3, energy)
+
+// One collide-and-stream update of the AA store `f` (element type given by
+// `storage`): parity 0 reads and writes the cell's own slots (writing the
+// post-collision population i into slot opp(i)); parity 1 reads slot opp(i)
+// of x - xi_i and writes slot i of x + xi_i.
+cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
+                        int parity, cudaStream_t st);
+
+// f = f0 + f1 (mode 1) or f0 (mode 0) from device fields rho [N], u [D][N].
+cudaError_t launch_init(int q, int storage, int model, void *f, const Grid &g, const float *rho,
+                        const float *u, float tau, int mode, cudaStream_t st);
+
+// Logical shifted populations (natural order) to / from float32 [Q][N].
+cudaError_t launch_get_populations(int q, int storage, const void *f, const Grid &g, int parity,
+                                   float *dst, cudaStream_t st);
+cudaError_t launch_set_populations(int q, int storage, void *f, const Grid &g, const float *src,
+                                   cudaStream_t st);
+
+// rho [N], u [D][N], pi1 [3|6][N]; NULL pointers skip the field.
+cudaError_t launch_moments(int q, int storage, const void *f, const Grid &g, int parity,
+                           float *rho, float *u, float *pi1, cudaStream_t st);
+
+// Deterministic FP64 reduction of (sum drho, sum rho u, 0.5 sum rho |u|^2)
+// into partials [kRedBlocks][kRedValues], then into out[kRedValues].
+cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g, int parity,
+                               double *partials, double *out, cudaStream_t st);
+
+// 0.5 sum |curl u|^2 from a velocity field u [D][N] (central differences),
+// reduced through partials [kRedBlocks] into out[0].
+cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
+                             cudaStream_t st);
+
+}  // namespace lbrr

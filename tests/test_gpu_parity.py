@@ -1,0 +1,210 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances (float32 arithmetic and storage):
+  * one update:  max over cells and i of |f_gpu - f_oracle| / w_i <= 1e-6
+  * 1000 updates: relative L2 error of u <= 1e-5 and of rho <= 1e-6
+Inputs are seeded and rounded to float32 before both sides see them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _common import f64_state, max_rel_to_weight, rel_l2, shifted, weights
+from paper_1505_06900_gb300 import binding as B
+from paper_1505_06900_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+ONE_STEP_TOL = 1e-6
+
+# shapes span several 128-wide x tiles with a ragged tail, and non-cubic extents
+CASES = [
+    (O.D2Q9, (300, 7, 1)),
+    (O.D2Q9, (5, 3, 1)),
+    (O.D3Q27, (150, 6, 5)),
+    (O.D3Q27, (3, 4, 5)),
+]
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _random_state(lattice, shape, seed, amp=0.05):
+    _, q = O.dims_of(lattice)
+    return W.random_populations(q, shape, seed, amp).astype(np.float32)
+
+
+def _solver(lattice, shape, tau, storage=B.STORE_F32, collision=B.COLLIDE_RR):
+    return B.Solver(lattice, shape, tau, storage=storage, collision=collision)
+
+
+@pytest.mark.parametrize("lattice,shape", CASES)
+@pytest.mark.parametrize("collision", [B.COLLIDE_RR, B.COLLIDE_REG2])
+def test_steps_match_oracle(lattice, shape, collision):
+    """Updates 1, 2 and 3 (both AA kernels) against the oracle's pull update."""
+    tau = 0.62
+    df = _random_state(lattice, shape, seed=100 + lattice)
+    variant = O.RR if collision == B.COLLIDE_RR else O.REG2
+    with _solver(lattice, shape, tau, collision=collision) as s:
+        s.set_populations(_cuda(df))
+        f = f64_state(lattice, df)
+        for k in range(1, 4):
+            s.step(1)
+            got = s.populations().cpu().numpy()
+            f = O.step(lattice, shape, tau, f, 1, variant)
+            err = max_rel_to_weight(lattice, got, shifted(lattice, f))
+            assert err <= ONE_STEP_TOL, (k, err)
+
+
+@pytest.mark.parametrize("lattice,shape", CASES[:3:2])
+def test_moments_after_even_and_odd_updates(lattice, shape):
+    d, _ = O.dims_of(lattice)
+    tau = 0.75
+    df = _random_state(lattice, shape, seed=7)
+    with _solver(lattice, shape, tau) as s:
+        s.set_populations(_cuda(df))
+        f = f64_state(lattice, df)
+        for k in range(3):
+            rho, u, p = (t.cpu().numpy() for t in s.moments())
+            r0, u0, p0 = O.fields(lattice, shape, f)
+            assert np.max(np.abs(rho - r0)) < 1e-6
+            assert np.max(np.abs(u - u0)) < 1e-6
+            assert np.max(np.abs(p - p0)) < 1e-6
+            s.step(1)
+            f = O.step(lattice, shape, tau, f, 1)
+
+
+@pytest.mark.parametrize("lattice,shape", CASES[:3:2])
+@pytest.mark.parametrize("mode", [B.INIT_EQ, B.INIT_EQ_NEQ_FD])
+def test_init_matches_oracle(lattice, shape, mode):
+    d, _ = O.dims_of(lattice)
+    rho, u = W.as_f32(*W.random_field(shape, d, seed=5))
+    with _solver(lattice, shape, 0.7) as s:
+        s.init_fields(_cuda(rho), _cuda(u), mode)
+        got = s.populations().cpu().numpy()
+    f = O.init(lattice, shape, 0.7, rho, u, mode)
+    assert max_rel_to_weight(lattice, got, shifted(lattice, f)) <= ONE_STEP_TOL
+
+
+def test_taylor_green_2d_1000_steps():
+    """D2Q9 128^2 Taylor-Green vortex, Re = 100, 1000 updates vs the oracle."""
+    n, u0 = 128, 0.05
+    tau = W.taylor_green_2d_tau(n, u0)
+    rho, u = W.as_f32(*W.taylor_green_2d(n, u0))
+    shape = (n, n, 1)
+    with _solver(O.D2Q9, shape, tau) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(1000)
+        r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
+    f = O.step(O.D2Q9, shape, tau, O.init(O.D2Q9, shape, tau, rho, u), 1000)
+    r_o, u_o, _ = O.fields(O.D2Q9, shape, f)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(r_g, r_o) <= 1e-6
+
+
+def test_taylor_green_3d_1000_steps():
+    """D3Q27 Taylor-Green vortex (Ma = 0.1, Re = 1600) on 24^3, 1000 updates."""
+    n, mach = 24, 0.1
+    tau = W.taylor_green_3d_tau(n, mach)
+    rho, u = W.as_f32(*W.taylor_green_3d(n, mach))
+    shape = (n, n, n)
+    with _solver(O.D3Q27, shape, tau) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(1000)
+        r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
+    f = O.step(O.D3Q27, shape, tau, O.init(O.D3Q27, shape, tau, rho, u), 1000)
+    r_o, u_o, _ = O.fields(O.D3Q27, shape, f)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(r_g, r_o) <= 1e-6
+
+
+@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (64, 48, 1)), (O.D3Q27, (20, 16, 12))])
+def test_diagnostics_and_enstrophy(lattice, shape):
+    d, _ = O.dims_of(lattice)
+    rho, u = W.as_f32(*W.random_field(shape, d, seed=9, a_u=0.03))
+    tau = 0.8
+    with _solver(lattice, shape, tau) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(3)
+        dg = s.diagnostics()
+        en = s.enstrophy()
+        df = s.populations().cpu().numpy()
+    f = O.step(lattice, shape, tau, O.init(lattice, shape, tau, rho, u), 3)
+    dref = O.diagnostics(lattice, shape, f)
+    assert abs(dg[0] - dref[0]) <= 1e-9 * dref[0]
+    assert np.allclose(dg[1:1 + d], dref[1:1 + d], rtol=0, atol=1e-5)
+    assert abs(dg[-1] / dref[-1] - 1) < 1e-5
+    assert abs(en / O.enstrophy(lattice, shape, f) - 1) < 1e-4
+    # deterministic: the same state gives bit-identical diagnostics
+    with _solver(lattice, shape, tau) as s:
+        s.set_populations(_cuda(df))
+        a, b = s.diagnostics(), s.diagnostics()
+        assert np.array_equal(a, b)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    shape = (40, 12, 10)
+    rho, u = W.as_f32(*W.random_field(shape, 3, seed=3))
+    with _solver(O.D3Q27, shape, 0.6) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(7)
+        buf = torch.empty(s.state_bytes(), dtype=torch.uint8, device="cuda")
+        par = s.get_state(buf)
+        assert par == 1
+        s.step(5)
+        a = s.populations().cpu().numpy()
+        s.set_state(buf, par)
+        s.step(5)
+        b = s.populations().cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_step_zero_and_argument_errors():
+    shape = (16, 8, 1)
+    with _solver(O.D2Q9, shape, 0.7) as s:
+        df = _random_state(O.D2Q9, shape, 1)
+        s.set_populations(_cuda(df))
+        s.step(0)
+        assert np.array_equal(s.populations().cpu().numpy(), df)
+        with pytest.raises(B.LBError) as e:
+            s.step(-1)
+        assert e.value.code == B.LB_EINVAL
+        # a failed call leaves the state unchanged
+        assert np.array_equal(s.populations().cpu().numpy(), df)
+
+
+def test_divergence_is_reported():
+    """A non-finite population makes the diagnostics return LB_EDIVERGED."""
+    shape = (8, 8, 1)
+    df = np.zeros((9, 1, 8, 8), np.float32)
+    df[3, 0, 2, 2] = np.nan
+    with _solver(O.D2Q9, shape, 0.7) as s:
+        s.set_populations(_cuda(df))
+        with pytest.raises(B.LBError) as e:
+            s.diagnostics()
+        assert e.value.code == B.LB_EDIVERGED
+
+
+def test_run_host_matches_device_path():
+    n = 64
+    rho, u = W.as_f32(*W.taylor_green_2d(n, 0.05))
+    tau = 0.6
+    shape = (n, n, 1)
+    rho_o = np.zeros((1, n, n), np.float32)
+    u_o = np.zeros((2, 1, n, n), np.float32)
+    diag = np.zeros(4)
+    with _solver(O.D2Q9, shape, tau) as s:
+        s.run_host(rho.astype(np.float32), u.astype(np.float32), 25, rho_out=rho_o, u_out=u_o,
+                   diag_out=diag)
+    with _solver(O.D2Q9, shape, tau) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(25)
+        r, uu, _ = (t.cpu().numpy() for t in s.moments())
+        d2 = s.diagnostics()
+    assert np.array_equal(rho_o[0], r) and np.array_equal(u_o, uu)
+    assert np.array_equal(diag, d2)
