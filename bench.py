@@ -1,0 +1,374 @@
+"""Throughput of the recursive-regularized BGK collide-and-stream step on GB300.
+
+Default workload (N=1): D3Q27 recursive-regularized BGK, FP32 storage, fully
+periodic 512^3 Taylor-Green vortex (Ma = 0.1, Re = 1600), AA-pattern store in
+HBM (14.5 GB, far larger than L2). One timed "step" is one full update of the
+grid (gather, moments, recursive reconstruction, collision, scatter), with the
+FP64 mass/momentum/energy reduction every 50 steps. Prints one JSON line:
+GLUPS (10^9 cell updates per second), the HBM roofline of the step kernel, an
+end-to-end figure through host buffers, FP16/BF16 storage variants, and the
+FP64 CPU oracle timed on the host cores on a bounded sample.
+
+Multi-GPU: replicas only. Each rank runs its own 512^3 domain (the path has no
+data exchange between replicas), so the figure is weak scaling.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 512] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUPS & %HBM roofline, D3Q27 RR: FP32 vs FP16-store vs learned at fixed error"
+UNIT = "GLUPS"
+DIAG_EVERY = 50
+MACH, RE = 0.1, 1600.0
+
+# DRAM traffic of one step-kernel launch from an ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
+# taken on; reported as null when the sources have changed since.
+TRAFFIC = {}
+
+KERNEL_SOURCES = ["paper_1505_06900_gb300/csrc/lbrr_step.cu",
+                  "paper_1505_06900_gb300/csrc/lbrr_device.cuh"]
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- distributed --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    import torch.distributed as dist
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+# -------------------------------------------------------------- reference --
+def oracle_sample(steps: int, warmup: int, n_sample: int, threads: int | None = None):
+    """Time the FP64 CPU oracle on a D3Q27 Taylor-Green vortex of n_sample^3
+    cells (a bounded sample of the 512^3 workload, same Ma and Re scaling)."""
+    import oracle as O
+    from paper_1505_06900_gb300 import workloads as W
+    O.build()
+    if threads:
+        O.set_num_threads(threads)
+    shape = (n_sample,) * 3
+    tau = W.taylor_green_3d_tau(n_sample, MACH, RE)
+    rho, u = W.as_f32(*W.taylor_green_3d(n_sample, MACH))
+    f = O.init(O.D3Q27, shape, tau, rho, u)
+    if warmup:
+        f = O.step(O.D3Q27, shape, tau, f, warmup)
+    t0 = time.perf_counter()
+    O.step(O.D3Q27, shape, tau, f, steps)
+    dt = time.perf_counter() - t0
+    cells = n_sample ** 3
+    return {"value": cells * steps / dt / 1e9, "unit": UNIT, "cores": O.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"D3Q27 Taylor-Green {n_sample}^3 (Ma {MACH}, Re {RE:g}), {steps} "
+                      f"oracle updates, FP64, OpenMP over cells"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    n_sample = 32
+    res = oracle_sample(args.steps, args.warmup, n_sample)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * res["seconds"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"D3Q27 RR Taylor-Green {n_sample}^3 sample of the 512^3 "
+                               f"workload (FP64 CPU oracle)", "lattice": "D3Q27",
+                   "grid": [n_sample] * 3, "parallelism": "replicas"},
+        "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm --
+def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_every, stream,
+                 sync_all, sampler=None):
+    """Warm up, then time `steps` updates; returns timing and per-launch data."""
+    s = B.Solver(B.D3Q27, (n, n, n), tau, storage=storage, stream=stream)
+    try:
+        s.init_fields(rho_d, u_d)
+        s.step(warmup)
+        for _ in range(max(1, warmup // diag_every)):
+            s.diagnostics()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        sync_all()
+        torch.cuda.synchronize()
+        launches = 0
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            with torch.cuda.stream(stream):
+                t_start.record(stream)
+                for k in range(steps):
+                    ev[k][0].record(stream)
+                    s.step(1)
+                    ev[k][1].record(stream)
+                    launches += 1
+                    if (k + 1) % diag_every == 0:
+                        s.diagnostics()
+                        launches += 2
+                t_end.record(stream)
+            torch.cuda.synchronize()
+        sync_all()
+        total_ms = t_start.elapsed_time(t_end)
+        kern_ms = [a.elapsed_time(b) for a, b in ev]
+        diag = s.diagnostics()
+        return {"total_ms": total_ms, "kernel_ms": statistics.mean(kern_ms),
+                "kernel_ms_median": statistics.median(kern_ms), "launches": launches,
+                "diag": diag.tolist(), "bytes_per_update": s.info()["bytes_per_update"]}
+    finally:
+        s.close()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_1505_06900_gb300 import binding as B
+    from paper_1505_06900_gb300 import build as build_mod
+    from paper_1505_06900_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(ws, "nccl")
+
+    def sync_all():
+        if dist:
+            dist.barrier()
+
+    if rank == 0:
+        build_mod.build()
+    sync_all()
+    B.load()
+
+    n = args.n
+    tau = W.taylor_green_3d_tau(n, MACH, RE)
+    rho, u = W.taylor_green_3d(n, MACH)
+    rho32 = np.ascontiguousarray(rho, dtype=np.float32)
+    u32 = np.ascontiguousarray(u, dtype=np.float32)
+    rho_d = torch.from_numpy(rho32).cuda()
+    u_d = torch.from_numpy(u32).cuda()
+    stream = torch.cuda.Stream()
+    cells = n ** 3
+
+    sampler = ClockSampler(local)
+    main = time_variant(B, torch, n, B.STORE_F32, args.steps, args.warmup, tau, rho_d, u_d,
+                        DIAG_EVERY, stream, sync_all, sampler)
+    variants = {}
+    if not args.skip_variants:
+        for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
+            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                             DIAG_EVERY, stream, sync_all)
+            variants[name] = {
+                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                "bytes_per_update": r["bytes_per_update"],
+                "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
+            }
+
+    # end to end through host buffers (pinned), one lb_run_host call of K steps
+    rho_h = torch.from_numpy(rho32).pin_memory()
+    u_h = torch.from_numpy(u32).pin_memory()
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    diag_h = np.zeros(5)
+    with B.Solver(B.D3Q27, (n, n, n), tau, stream=stream) as s:
+        s.run_host(rho_h, u_h, 2, rho_out=rho_o, u_out=u_o, diag_out=diag_h)  # warm-up
+        sync_all()
+        t0 = time.perf_counter()
+        s.run_host(rho_h, u_h, args.steps, rho_out=rho_o, u_out=u_o, diag_out=diag_h)
+        e2e_s = time.perf_counter() - t0
+        sync_all()
+    h2d = (rho32.nbytes + u32.nbytes)
+    d2h = (rho32.nbytes + u32.nbytes) + diag_h.nbytes
+
+    # max over ranks
+    times = torch.tensor([main["total_ms"], main["kernel_ms"], e2e_s], dtype=torch.float64,
+                         device="cuda")
+    if dist:
+        dist.all_reduce(times, op=dist.ReduceOp.MAX)
+    total_ms, kernel_ms, e2e_s = times.tolist()
+
+    if rank != 0:
+        return 0
+
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    if "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    bpu = main["bytes_per_update"]
+    achieved = bpu * cells / (kernel_ms * 1e-3) / 1e9
+    sha = kernel_sha()
+    tr = TRAFFIC.get(f"d3q27_f32_{n}")
+    traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == sha else None
+
+    cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample)
+    clocks = sampler.summary()
+    value = ws * cells * args.steps / (total_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": f"D3Q27 recursive-regularized BGK, FP32 AA store, periodic {n}^3 "
+                        f"Taylor-Green vortex Ma={MACH} Re={RE:g}",
+            "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau": tau,
+            "diag_every": DIAG_EVERY, "bytes_per_update": bpu,
+            "l2": f"inputs larger than L2 ({bpu // 2 * cells / 1e9:.1f} GB store)",
+            "parallelism": "replicas" if ws > 1 else "single",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "rr_step_kernel<27,f32,RR>", "peak_source": peak_src,
+                     "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": bpu * cells},
+        "variants": variants,
+        "e2e": {"value": ws * cells * args.steps / e2e_s / 1e9, "unit": UNIT,
+                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                "scope": "lb_run_host: pinned upload of rho,u, init, K updates, download of "
+                         "rho,u and diagnostics"},
+        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "gpu_launches": main["launches"],
+        "clocks": clocks,
+        "kernel_sha": sha,
+        "diagnostics_end": main["diag"],
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--cpu-sample", type=int, default=64)
+    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--skip-variants", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

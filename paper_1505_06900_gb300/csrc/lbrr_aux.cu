@@ -61,6 +61,9 @@ __global__ void __launch_bounds__(kAuxThreads)
   m.ux = u[cell];
   m.uy = u[n + cell];
   m.uz = D == 3 ? u[2 * n + cell] : 0.0f;
+  m.jx = m.rho * m.ux;
+  m.jy = m.rho * m.uy;
+  m.jz = m.rho * m.uz;
   m.pxx = m.pxy = m.pxz = m.pyy = m.pyz = m.pzz = 0.0f;
   if (mode == 1) {
     // du[b][a] = d u_b / d x_a by periodic central differences
@@ -196,12 +199,12 @@ __global__ void __launch_bounds__(kRedThreads)
     float df[Q];
     load_logical<Q, S>(f, g, parity, x, y, z, df);
     const Macro m = Lattice<Q>::moments(df);
-    const double r = m.rho, ux = m.ux, uy = m.uy, uz = m.uz;
+    const double jx = m.jx, jy = m.jy, jz = m.jz;
     acc[0] += (double)m.drho;
-    acc[1] += r * ux;
-    acc[2] += r * uy;
-    acc[3] += r * uz;
-    acc[4] += 0.5 * r * (ux * ux + uy * uy + uz * uz);
+    acc[1] += jx;
+    acc[2] += jy;
+    acc[3] += jz;
+    acc[4] += 0.5 * (jx * jx + jy * jy + jz * jz) / (double)m.rho;
   }
   block_sum<kRedValues>(acc, partials + (long long)blockIdx.x * kRedValues);
 }

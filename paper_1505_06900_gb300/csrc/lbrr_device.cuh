@@ -15,10 +15,12 @@
 //    f = (T (x) T (x) T) C with the 1-D map
 //      T(c0, c1, c2)(xi) = w_xi (c0 + 3 xi c1 + 9/2 (xi^2 - 1/3) c2).
 // The coefficient tensor of f0 + (1 - 1/tau) f1 is a sum of three rank-one
-// terms along x (u_x powers, their second and first u_x derivatives), so the
-// synthesis runs x first on those terms and then applies T along y and z.
+// terms along x (u_x powers, their second and first u_x derivatives), which
+// is how it is assembled; T is then applied along x, y and z.
 // All values carried are shifted by the rest state (df = f - w), which keeps
-// float32 round-off relative to the deviations rather than to w.
+// float32 round-off relative to the deviations rather than to w, and the
+// conserved coefficients (rho - 1 and rho u) are the moments themselves, so
+// that round-off does not make mass or momentum drift from step to step.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -97,7 +99,9 @@ struct Storage<2> {
 // shifted populations: rho - 1 = sum df, rho u = sum xi df, and
 // sum xi xi f = sum xi xi df + cs2 I (the rest state's second moment).
 struct Macro {
-  float drho, rho, ux, uy, uz;
+  float drho, rho;          // rho - 1 and rho
+  float jx, jy, jz;         // momentum rho u (the first moments themselves)
+  float ux, uy, uz;
   float pxx, pxy, pxz, pyy, pyz, pzz;
 };
 
@@ -120,9 +124,11 @@ __device__ __forceinline__ Macro moments_d2q9(const float (&f)[9]) {
   const float m20 = s2[0] + s2[1] + s2[2];
   m.drho = m00;
   m.rho = 1.0f + m00;
-  const float inv = 1.0f / m.rho;
-  m.ux = m10 * inv;
-  m.uy = m01 * inv;
+  m.jx = m10;
+  m.jy = m01;
+  m.jz = 0.0f;
+  m.ux = m10 / m.rho;
+  m.uy = m01 / m.rho;
   m.uz = 0.0f;
   m.pxx = m20 - kCs2 * m00 - m10 * m.ux;
   m.pxy = m11 - m10 * m.uy;
@@ -166,10 +172,12 @@ __device__ __forceinline__ Macro moments_d3q27(const float (&f)[27]) {
   Macro m;
   m.drho = m000;
   m.rho = 1.0f + m000;
-  const float inv = 1.0f / m.rho;
-  m.ux = m100 * inv;
-  m.uy = m010 * inv;
-  m.uz = m001 * inv;
+  m.jx = m100;
+  m.jy = m010;
+  m.jz = m001;
+  m.ux = m100 / m.rho;
+  m.uy = m010 / m.rho;
+  m.uz = m001 / m.rho;
   m.pxx = m200 - kCs2 * m000 - m100 * m.ux;
   m.pyy = m020 - kCs2 * m000 - m010 * m.uy;
   m.pzz = m002 - kCs2 * m000 - m001 * m.uz;
@@ -189,123 +197,32 @@ __device__ __forceinline__ void synth1(float c0, float c1, float c2, float &om, 
   om = 0.5f * (q - c1);
 }
 
-// Per-axis factors at xi = -1, 0, +1 for velocity component u:
-//  dg = g(xi, u) - w_xi, with g the 1-D equilibrium T(1, u, u^2);
-//  dd = T(0, 1, 2u)  (first u-derivative of g);  hh = T(0, 0, 1) = (1/2, -1, 1/2).
-struct Axis {
-  float dg[3], dd[3];
-};
-__device__ __forceinline__ Axis axis_factors(float u) {
-  Axis a;
-  const float uu = u * u;
-  a.dg[0] = 0.5f * (uu - u);
-  a.dg[1] = -uu;
-  a.dg[2] = 0.5f * (uu + u);
-  a.dd[0] = u - 0.5f;
-  a.dd[1] = -2.0f * u;
-  a.dd[2] = u + 0.5f;
-  return a;
-}
-
 // Shifted post-collision populations of a D2Q9 cell (RR, Sec. 3.4):
 // df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1 rebuilds f0 + f1).
+// Coefficient of x^a y^b: C = px[a] Q1[b] + h[a] Q2[b] + dx[a] Q3[b] with
+// px = (1, ux, ux^2), h = (0, 0, 1), dx = (0, 1, 2 ux) (powers of ux and their
+// second and first ux-derivatives) and the y-vectors
+//   Q1 = rho (1, uy, uy^2) + om1 Pi_yy (0, 0, 1)
+//   Q2 = om1 Pi_xx (1, uy, uy^2),   Q3 = om1 Pi_xy (0, 1, 2 uy).
+// The conserved coefficients are then set from the moments themselves
+// (C_00 = rho - 1, C_10 = rho ux, C_01 = rho uy), so that mass and momentum
+// pass through the update with no other rounding than the synthesis'.
 __device__ __forceinline__ void synth_rr_d2q9(const Macro &m, float om1, float (&f)[9]) {
-  const Axis ax = axis_factors(m.ux);
-  const float uy = m.uy, uyy = uy * uy;
+  const float ux = m.ux, uy = m.uy, uyy = uy * uy;
   const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pxy = om1 * m.pxy;
-  // y-coefficient vectors of the three x-terms (b = 0, 1, 2):
-  //  Q1 = rho (1, uy, uy^2) + Pi_yy (0, 0, 1)   [paired with g_x]
-  //  Q2 = Pi_xx (1, uy, uy^2)                    [paired with hh]
-  //  Q3 = Pi_xy (0, 1, 2 uy)                     [paired with dd_x]
   const float q1[3] = {m.rho, m.rho * uy, fmaf(m.rho, uyy, pyy)};
   const float q2[3] = {pxx, pxx * uy, pxx * uyy};
   const float q3[3] = {0.0f, pxy, 2.0f * pxy * uy};
-#pragma unroll
-  for (int ix = 0; ix < 3; ++ix) {
-    const float wx = w1(ix), gx = wx + ax.dg[ix], hx = hh1(ix), dx = ax.dd[ix];
-    // b = 0 carries the shift: g_x rho - w_x = w_x drho + dg_x rho
-    const float r0 = fmaf(hx, q2[0], fmaf(ax.dg[ix], m.rho, wx * m.drho));
-    const float r1 = fmaf(dx, q3[1], fmaf(hx, q2[1], gx * q1[1]));
-    const float r2 = fmaf(dx, q3[2], fmaf(hx, q2[2], gx * q1[2]));
-    float om, oz, op;
-    synth1(r0, r1, r2, om, oz, op);
-    f[ix] = om;
-    f[ix + 3] = oz;
-    f[ix + 6] = op;
-  }
-}
-
-// Shifted post-collision populations of a D3Q27 cell (RR, Sec. 3.4).
-__device__ __forceinline__ void synth_rr_d3q27(const Macro &m, float om1, float (&f)[27]) {
-  const Axis ax = axis_factors(m.ux);
-  const float uy = m.uy, uz = m.uz;
-  const float py[3] = {1.0f, uy, uy * uy}, pz[3] = {1.0f, uz, uz * uz};
-  const float dy[3] = {0.0f, 1.0f, 2.0f * uy}, dz[3] = {0.0f, 1.0f, 2.0f * uz};
-  const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pzz = om1 * m.pzz;
-  const float pxy = om1 * m.pxy, pxz = om1 * m.pxz, pyz = om1 * m.pyz;
-  // (y, z) coefficient matrices of the three x-terms, index [b][c]:
-  //  Q1 = rho py pz + Pi_yy h py' + Pi_zz py h' + Pi_yz dy dz   [with g_x]
-  //  Q2 = Pi_xx py pz                                            [with hh]
-  //  Q3 = Pi_xy dy pz + Pi_xz py dz                              [with dd_x]
-  float q1[3][3], q2[3][3], q3[3][3];
+  float c[3][3];  // [a][b]
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float pp = py[b] * pz[c];
-      float v = m.rho * pp;
-      if (b == 2) v = fmaf(pyy, pz[c], v);
-      if (c == 2) v = fmaf(pzz, py[b], v);
-      if (b > 0 && c > 0) v = fmaf(pyz, dy[b] * dz[c], v);
-      q1[b][c] = v;
-      q2[b][c] = pxx * pp;
-      float w = 0.0f;
-      if (b > 0) w = fmaf(pxy, dy[b] * pz[c], w);
-      if (c > 0) w = fmaf(pxz, py[b] * dz[c], w);
-      q3[b][c] = w;
-    }
+    c[0][b] = q1[b];
+    c[1][b] = fmaf(ux, q1[b], q3[b]);
+    c[2][b] = fmaf(ux * ux, q1[b], fmaf(2.0f * ux, q3[b], q2[b]));
   }
-#pragma unroll
-  for (int ix = 0; ix < 3; ++ix) {
-    const float wx = w1(ix), gx = wx + ax.dg[ix], hx = hh1(ix), dx = ax.dd[ix];
-    float r[3][3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (b == 0 && c == 0) {
-          // shifted entry: g_x rho - w_x = w_x drho + dg_x rho (q3[0][0] = 0)
-          r[0][0] = fmaf(hx, q2[0][0], fmaf(ax.dg[ix], m.rho, wx * m.drho));
-        } else {
-          r[b][c] = fmaf(dx, q3[b][c], fmaf(hx, q2[b][c], gx * q1[b][c]));
-        }
-      }
-    }
-    // synthesis along y for each z-coefficient c, then along z
-    float s[3][3];  // [iy][c]
-#pragma unroll
-    for (int c = 0; c < 3; ++c) synth1(r[0][c], r[1][c], r[2][c], s[0][c], s[1][c], s[2][c]);
-#pragma unroll
-    for (int iy = 0; iy < 3; ++iy) {
-      float om, oz, op;
-      synth1(s[iy][0], s[iy][1], s[iy][2], om, oz, op);
-      f[ix + 3 * iy] = om;
-      f[ix + 3 * iy + 9] = oz;
-      f[ix + 3 * iy + 18] = op;
-    }
-  }
-}
-
-// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
-// coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
-__device__ __forceinline__ void synth_reg2_d2q9(const Macro &m, float om1, float (&f)[9]) {
-  float c[3][3] = {};  // [a][b] coefficient of x^a y^b
   c[0][0] = m.drho;
-  c[1][0] = m.rho * m.ux;
-  c[0][1] = m.rho * m.uy;
-  c[2][0] = fmaf(om1, m.pxx, m.rho * m.ux * m.ux);
-  c[0][2] = fmaf(om1, m.pyy, m.rho * m.uy * m.uy);
-  c[1][1] = fmaf(om1, m.pxy, m.rho * m.ux * m.uy);
+  c[1][0] = m.jx;
+  c[0][1] = m.jy;
   float s[3][3];  // [ix][b]
 #pragma unroll
   for (int b = 0; b < 3; ++b) synth1(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
@@ -313,18 +230,9 @@ __device__ __forceinline__ void synth_reg2_d2q9(const Macro &m, float om1, float
   for (int ix = 0; ix < 3; ++ix) synth1(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
 }
 
-__device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, float (&f)[27]) {
-  float c[3][3][3] = {};  // [a][b][c]
-  c[0][0][0] = m.drho;
-  c[1][0][0] = m.rho * m.ux;
-  c[0][1][0] = m.rho * m.uy;
-  c[0][0][1] = m.rho * m.uz;
-  c[2][0][0] = fmaf(om1, m.pxx, m.rho * m.ux * m.ux);
-  c[0][2][0] = fmaf(om1, m.pyy, m.rho * m.uy * m.uy);
-  c[0][0][2] = fmaf(om1, m.pzz, m.rho * m.uz * m.uz);
-  c[1][1][0] = fmaf(om1, m.pxy, m.rho * m.ux * m.uy);
-  c[1][0][1] = fmaf(om1, m.pxz, m.rho * m.ux * m.uz);
-  c[0][1][1] = fmaf(om1, m.pyz, m.rho * m.uy * m.uz);
+// Separable synthesis of a 3x3x3 coefficient tensor c[a][b][c] (x, y, z
+// powers) into the 27 populations, i = ix + 3 iy + 9 iz.
+__device__ __forceinline__ void synth_tensor_d3q27(const float (&c)[3][3][3], float (&f)[27]) {
   float sx[3][3][3];  // [ix][b][c]
 #pragma unroll
   for (int b = 0; b < 3; ++b)
@@ -342,6 +250,78 @@ __device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, floa
       synth1(sy[iy][0], sy[iy][1], sy[iy][2], f[ix + 3 * iy], f[ix + 3 * iy + 9],
              f[ix + 3 * iy + 18]);
   }
+}
+
+// Shifted post-collision populations of a D3Q27 cell (RR, Sec. 3.4). The
+// coefficient of x^a y^b z^c is C = px[a] Q1[b][c] + h[a] Q2[b][c] +
+// dx[a] Q3[b][c] (px, h, dx as in 2D) with the (y, z) matrices
+//   Q1 = rho py pz + om1 (Pi_yy h_y pz + Pi_zz py h_z + Pi_yz dy dz)
+//   Q2 = om1 Pi_xx py pz,   Q3 = om1 (Pi_xy dy pz + Pi_xz py dz),
+// i.e. f0's coefficients rho ux^a uy^b uz^c plus om1 times the recursion's
+// pair sums; the conserved coefficients come from the moments directly.
+__device__ __forceinline__ void synth_rr_d3q27(const Macro &m, float om1, float (&f)[27]) {
+  const float ux = m.ux, uy = m.uy, uz = m.uz;
+  const float py[3] = {1.0f, uy, uy * uy}, pz[3] = {1.0f, uz, uz * uz};
+  const float dy[3] = {0.0f, 1.0f, 2.0f * uy}, dz[3] = {0.0f, 1.0f, 2.0f * uz};
+  const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pzz = om1 * m.pzz;
+  const float pxy = om1 * m.pxy, pxz = om1 * m.pxz, pyz = om1 * m.pyz;
+  const float uxx = ux * ux, ux2 = 2.0f * ux;
+  float c[3][3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      const float pp = py[b] * pz[cc];
+      float q1 = m.rho * pp;
+      if (b == 2) q1 = fmaf(pyy, pz[cc], q1);
+      if (cc == 2) q1 = fmaf(pzz, py[b], q1);
+      if (b > 0 && cc > 0) q1 = fmaf(pyz, dy[b] * dz[cc], q1);
+      const float q2 = pxx * pp;
+      float q3 = 0.0f;
+      if (b > 0) q3 = fmaf(pxy, dy[b] * pz[cc], q3);
+      if (cc > 0) q3 = fmaf(pxz, py[b] * dz[cc], q3);
+      c[0][b][cc] = q1;
+      c[1][b][cc] = fmaf(ux, q1, q3);
+      c[2][b][cc] = fmaf(uxx, q1, fmaf(ux2, q3, q2));
+    }
+  }
+  c[0][0][0] = m.drho;
+  c[1][0][0] = m.jx;
+  c[0][1][0] = m.jy;
+  c[0][0][1] = m.jz;
+  synth_tensor_d3q27(c, f);
+}
+
+// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
+// coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
+__device__ __forceinline__ void synth_reg2_d2q9(const Macro &m, float om1, float (&f)[9]) {
+  float c[3][3] = {};  // [a][b] coefficient of x^a y^b
+  c[0][0] = m.drho;
+  c[1][0] = m.jx;
+  c[0][1] = m.jy;
+  c[2][0] = fmaf(om1, m.pxx, m.jx * m.ux);
+  c[0][2] = fmaf(om1, m.pyy, m.jy * m.uy);
+  c[1][1] = fmaf(om1, m.pxy, m.jx * m.uy);
+  float s[3][3];  // [ix][b]
+#pragma unroll
+  for (int b = 0; b < 3; ++b) synth1(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
+#pragma unroll
+  for (int ix = 0; ix < 3; ++ix) synth1(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
+}
+
+__device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, float (&f)[27]) {
+  float c[3][3][3] = {};  // [a][b][c]
+  c[0][0][0] = m.drho;
+  c[1][0][0] = m.jx;
+  c[0][1][0] = m.jy;
+  c[0][0][1] = m.jz;
+  c[2][0][0] = fmaf(om1, m.pxx, m.jx * m.ux);
+  c[0][2][0] = fmaf(om1, m.pyy, m.jy * m.uy);
+  c[0][0][2] = fmaf(om1, m.pzz, m.jz * m.uz);
+  c[1][1][0] = fmaf(om1, m.pxy, m.jx * m.uy);
+  c[1][0][1] = fmaf(om1, m.pxz, m.jx * m.uz);
+  c[0][1][1] = fmaf(om1, m.pyz, m.jy * m.uz);
+  synth_tensor_d3q27(c, f);
 }
 
 template <int Q>

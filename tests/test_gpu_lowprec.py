@@ -1,0 +1,100 @@
+"""FP16 / BF16 population storage: exact-rounding parity for one update and the
+error budget over many updates, against the FP64 oracle.
+
+The 16-bit stores hold g_i = (f_i - w_i) / w_i rounded to nearest even; all
+arithmetic is float32. One update: the stored result must be the oracle's
+post-collision g rounded to the storage type, within one unit in the last
+place of that type plus the float32 tolerance of the unrounded update
+(1e-6 relative to w_i, as for the FP32 store): near zero the spacing of BF16
+is far finer than float32 round-off of the O(0.1) terms that cancel there.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from _common import rel_l2, weights
+from paper_1505_06900_gb300 import binding as B
+from paper_1505_06900_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# error budget after 1000 updates of the D2Q9 128^2 Taylor-Green vortex against
+# the FP64 oracle (relative L2 of u and of rho), frozen at the first
+# measurement on GB300 (BF16: u 3.19e-3, rho 1.03e-4).
+BUDGET = {
+    B.STORE_F16: {"u": 1e-3, "rho": 1e-5},
+    B.STORE_BF16: {"u": 1e-2, "rho": 2e-4},
+}
+
+
+def round16(x: np.ndarray, storage: int) -> np.ndarray:
+    """Round-to-nearest-even of float values to FP16 or BF16, back in float64."""
+    x32 = torch.from_numpy(np.asarray(x, dtype=np.float32))
+    dt = torch.float16 if storage == B.STORE_F16 else torch.bfloat16
+    return x32.to(dt).to(torch.float64).numpy()
+
+
+def ulp16(x: np.ndarray, storage: int) -> np.ndarray:
+    """Spacing of the 16-bit format at |x|."""
+    mant, emin = (10, -14) if storage == B.STORE_F16 else (7, -126)
+    e = np.floor(np.log2(np.maximum(np.abs(x), 2.0 ** emin)))
+    return 2.0 ** (np.maximum(e, emin) - mant)
+
+
+def raw_store(g: np.ndarray, storage: int, parity: int, c: np.ndarray) -> "torch.Tensor":
+    """Raw 16-bit AA store holding the logical values g [Q, nz, ny, nx] at the
+    given parity: parity 0 keeps population i of x in slot i of x; parity 1
+    keeps it in slot opp(i) of x - xi_i."""
+    q = g.shape[0]
+    raw = np.empty_like(g)
+    for i in range(q):
+        if parity == 0:
+            raw[i] = g[i]
+        else:
+            raw[q - 1 - i] = np.roll(g[i], shift=(-c[i, 2], -c[i, 1], -c[i, 0]), axis=(0, 1, 2))
+    dt = torch.float16 if storage == B.STORE_F16 else torch.bfloat16
+    return torch.from_numpy(raw.astype(np.float32)).to(dt).contiguous().view(torch.uint8).cuda()
+
+
+@pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16])
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (260, 5, 1)), (O.D3Q27, (140, 5, 4))])
+def test_one_update_is_correctly_rounded(storage, parity, lattice, shape):
+    """Both AA kernels (the store is written at either parity from the host)."""
+    _, q = O.dims_of(lattice)
+    c, _ = O.lattice_tables(lattice)
+    w = weights(lattice).reshape(-1, 1, 1, 1)
+    df = W.random_populations(q, shape, seed=31 + parity, amp=0.05)
+    g_in = round16(df / w, storage)            # what the 16-bit store holds
+    f_ref = O.step(lattice, shape, 0.63, w * (1.0 + g_in), 1)
+    g_ref = f_ref / w - 1.0
+    with B.Solver(lattice, shape, 0.63, storage=storage) as s:
+        raw = raw_store(g_in, storage, parity, c)
+        assert raw.numel() == s.state_bytes()
+        s.set_state(raw, parity)
+        s.step(1)
+        g_gpu = s.populations().cpu().numpy().astype(np.float64) / w
+    err = np.abs(g_gpu - g_ref) / (ulp16(g_ref, storage) + 1e-6)
+    assert err.max() <= 1.0, err.max()
+
+
+@pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16])
+def test_error_budget_1000_updates(storage):
+    """D2Q9 128^2 Taylor-Green vortex, Re = 100: 16-bit storage error after
+    1000 updates, relative to the FP64 oracle."""
+    n, u0 = 128, 0.05
+    tau = W.taylor_green_2d_tau(n, u0)
+    rho, u = W.as_f32(*W.taylor_green_2d(n, u0))
+    shape = (n, n, 1)
+    with B.Solver(O.D2Q9, shape, tau, storage=storage) as s:
+        s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
+                      torch.from_numpy(u.astype(np.float32)).cuda())
+        s.step(1000)
+        r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
+    f = O.step(O.D2Q9, shape, tau, O.init(O.D2Q9, shape, tau, rho, u), 1000)
+    r_o, u_o, _ = O.fields(O.D2Q9, shape, f)
+    eu, er = rel_l2(u_g, u_o), rel_l2(r_g, r_o)
+    print(f"storage {storage}: u {eu:.3e} rho {er:.3e}")
+    assert eu <= BUDGET[storage]["u"]
+    assert er <= BUDGET[storage]["rho"]

@@ -206,5 +206,5 @@ def test_run_host_matches_device_path():
         s.step(25)
         r, uu, _ = (t.cpu().numpy() for t in s.moments())
         d2 = s.diagnostics()
-    assert np.array_equal(rho_o[0], r) and np.array_equal(u_o, uu)
+    assert np.array_equal(rho_o, r) and np.array_equal(u_o, uu)
     assert np.array_equal(diag, d2)
