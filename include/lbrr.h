@@ -159,6 +159,31 @@ LB_API int lb_run_host(lb_ctx *ctx, const float *rho_h, const float *u_h, int in
  * collision, number of steps taken, bytes moved per cell update. */
 LB_API int lb_info(const lb_ctx *ctx, long long *out);
 
+/* Largest grid (nx * ny * nz cells) that lb_diagnostics_static accepts. */
+#define LB_STATIC_MAX_CELLS 134217728LL /* 512^3 */
+
+/* The diagnostics of lb_diagnostics computed without allocating anything, for
+ * callers that cannot call cudaMalloc or cudaFree: those whose device memory
+ * is already reserved by another allocator, and those running beside a live
+ * simulation that must not take the device-wide synchronisation of cudaFree.
+ * The paper has no counterpart; this is a service of the library.
+ *
+ * store: device pointer to a raw population store of the given lattice, size,
+ * storage and AA parity, laid out as lb_get_state writes it. out: host memory,
+ * 2 + D doubles (mass, momentum, kinetic energy) as in lb_diagnostics.
+ * stream: cudaStream_t to order the work on (NULL: legacy default stream); the
+ * call synchronises it. The reduction's partial sums live in a fixed device
+ * array inside the library (1.25 MiB per GPU, held until the process exits),
+ * so grids above LB_STATIC_MAX_CELLS cells are rejected with LB_EINVAL. All
+ * calls on a device share that array: calls that overlap on the GPU race and
+ * must be serialised by the caller. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make it before any stream
+ * capture. Errors: LB_EINVAL (bad argument or grid too large), LB_ECUDA,
+ * LB_EDIVERGED (out filled, a value is not finite); lb_last_error(NULL) has
+ * the text. */
+LB_API int lb_diagnostics_static(int lattice, int nx, int ny, int nz, int storage, int parity,
+                                 const void *store, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,7 +42,9 @@ SIGNATURES = {
     "lb_set_state": (_i, [_vp, _vp, _i]),
     "lb_run_host": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "lb_info": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "lb_diagnostics_static": (_i, [_i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
 }
+LB_STATIC_MAX_CELLS = 134217728
 
 
 class LBOptions(ctypes.Structure):

@@ -106,6 +106,16 @@ int diagnostics(lb_ctx *c, double *out) {
 
 }  // namespace
 
+namespace lbrr {
+int report_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_create_err, sizeof g_create_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+}  // namespace lbrr
+
 extern "C" {
 
 int lb_create_ex(lb_ctx **out, const lb_options *opt) {

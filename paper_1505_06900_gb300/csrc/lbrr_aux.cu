@@ -352,6 +352,22 @@ cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g,
   return cudaGetLastError();
 }
 
+cudaError_t launch_diagnostics_blocks(int q, int storage, const void *f, const Grid &g,
+                                      int parity, int nblocks, double *partials, double *out,
+                                      cudaStream_t st) {
+  dispatch_qs(q, storage, [&](auto qc, auto sc) {
+    constexpr int Q_ = decltype(qc)::value;
+    constexpr int S_ = decltype(sc)::value;
+    using T = typename Storage<S_>::T;
+    diag_partial_kernel<Q_, S_><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T *>(f), g,
+                                                                 parity, partials);
+  });
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  finalize_kernel<<<1, kRedThreads, 0, st>>>(partials, nblocks, kRedValues, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
                              cudaStream_t st) {
   const int nb = red_blocks(g.n);

@@ -43,4 +43,14 @@ cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g,
 cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
                              cudaStream_t st);
 
+// As launch_diagnostics with the number of partial-sum blocks given by the
+// caller (partials must hold nblocks * kRedValues doubles); used by the
+// entry point that brings its own scratch.
+cudaError_t launch_diagnostics_blocks(int q, int storage, const void *f, const Grid &g,
+                                      int parity, int nblocks, double *partials, double *out,
+                                      cudaStream_t st);
+
+// Records a message for lb_last_error(NULL) on the calling thread.
+int report_error(int code, const char *fmt, ...);
+
 }  // namespace lbrr

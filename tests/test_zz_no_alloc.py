@@ -1,0 +1,73 @@
+"""lb_diagnostics_static: the diagnostics reduction for callers that cannot
+allocate device memory (their memory is reserved by another allocator, or they
+must not take the device-wide synchronisation of cudaFree beside a running
+simulation). It reads a caller-owned raw population store and keeps its
+partial sums in a fixed device array inside the library.
+
+The GPU test compares two calls in a row with lb_diagnostics on the same
+state, at the tolerances of the other diagnostics tests. This file is named to
+be collected last, and each test builds everything it needs, so it passes both
+alone in a fresh process and after the rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1505_06900_gb300 import binding as B
+from paper_1505_06900_gb300 import build as build_mod
+from paper_1505_06900_gb300 import workloads as W
+
+
+def _static(lib, s, buf, parity, storage, stream):
+    out = np.zeros(2 + s.d)
+    rc = lib.lb_diagnostics_static(s.lattice, s.nx, s.ny, s.nz, storage, parity, buf.data_ptr(),
+                                   out.ctypes.data, ctypes.c_void_p(stream.cuda_stream))
+    assert rc == B.LB_OK, lib.lb_last_error(None).decode()
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("lattice,shape,storage", [
+    (B.D3Q27, (40, 30, 20), B.STORE_F32),
+    (B.D2Q9, (300, 7, 1), B.STORE_F32),
+    (B.D3Q27, (24, 16, 12), B.STORE_F16),
+])
+def test_static_diagnostics_match_lb_diagnostics(lattice, shape, storage):
+    import torch
+    build_mod.build()
+    lib = B.load()
+    d = 2 if lattice == B.D2Q9 else 3
+    rho, u = W.as_f32(*W.random_field(shape, d, seed=21, a_u=0.03))
+    stream = torch.cuda.current_stream()
+    with B.Solver(lattice, shape, 0.7, storage=storage) as s:
+        s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
+                      torch.from_numpy(u.astype(np.float32)).cuda())
+        for nsteps in (3, 1):  # odd parity, then even
+            s.step(nsteps)
+            ref = s.diagnostics()
+            buf = torch.empty(s.state_bytes(), dtype=torch.uint8, device="cuda")
+            parity = s.get_state(buf)
+            first = _static(lib, s, buf, parity, storage, stream)
+            second = _static(lib, s, buf, parity, storage, stream)
+            for got in (first, second):
+                assert abs(got[0] - ref[0]) <= 1e-9 * ref[0]
+                assert np.allclose(got[1:1 + d], ref[1:1 + d], rtol=0, atol=1e-5)
+                assert abs(got[-1] / ref[-1] - 1) < 1e-5
+            # the array keeps the last call's contents; a repeated call on the
+            # same input reproduces the result exactly
+            assert np.array_equal(first, second)
+
+
+def test_static_diagnostics_rejects_grids_beyond_the_limit():
+    build_mod.build()
+    lib = B.load()
+    out = np.zeros(5)
+    dummy = ctypes.c_void_p(1)  # never dereferenced: the size check comes first
+    rc = lib.lb_diagnostics_static(B.D3Q27, 1024, 1024, 129, B.STORE_F32, 0, dummy,
+                                   out.ctypes.data, None)
+    assert rc == B.LB_EINVAL
+    msg = lib.lb_last_error(None).decode()
+    assert "LB_STATIC_MAX_CELLS" in msg and str(B.LB_STATIC_MAX_CELLS) in msg
+    rc = lib.lb_diagnostics_static(B.D2Q9, 16, 16, 2, B.STORE_F32, 0, dummy, out.ctypes.data, None)
+    assert rc == B.LB_EINVAL
