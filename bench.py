@@ -264,15 +264,14 @@ def run_gpu(args):
     main = time_variant(B, torch, n, B.STORE_F32, args.steps, args.warmup, tau, rho_d, u_d,
                         DIAG_EVERY, stream, sync_all, sampler)
     variants = {}
-    if not args.skip_variants:
-        for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
-            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                             DIAG_EVERY, stream, sync_all)
-            variants[name] = {
-                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
-                "bytes_per_update": r["bytes_per_update"],
-                "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
-            }
+    for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
+        r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                         DIAG_EVERY, stream, sync_all)
+        variants[name] = {
+            "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+            "bytes_per_update": r["bytes_per_update"],
+            "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
+        }
 
     # end to end through host buffers (pinned), one lb_run_host call of K steps
     rho_h = torch.from_numpy(rho32).pin_memory()
@@ -361,7 +360,6 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=64)
     ap.add_argument("--cpu-steps", type=int, default=30)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--skip-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

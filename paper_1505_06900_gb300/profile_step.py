@@ -1,0 +1,59 @@
+"""Small, self-contained run of the step kernel for profilers (ncu).
+
+    python -m paper_1505_06900_gb300.profile_step [--n 256] [--storage f32|f16|bf16]
+                                                  [--lattice 27|9] [--steps 6]
+
+Initialises a Taylor-Green vortex on an n^3 (D3Q27) or n^2 (D2Q9) periodic
+grid, runs `steps` updates through the C ABI and prints the elapsed time. At
+n = 256 the D3Q27 FP32 store is 1.8 GB: larger than L2, small enough for a
+multi-pass profiler capture.
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    from . import binding as B
+    from . import build as build_mod
+    from . import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--lattice", type=int, default=27, choices=[9, 27])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--steps", type=int, default=6)
+    args = ap.parse_args()
+    build_mod.build()
+    storage = {"f32": B.STORE_F32, "f16": B.STORE_F16, "bf16": B.STORE_BF16}[args.storage]
+    n = args.n
+    if args.lattice == 27:
+        shape = (n, n, n)
+        rho, u = W.taylor_green_3d(n, 0.1)
+        tau = W.taylor_green_3d_tau(n, 0.1)
+    else:
+        shape = (n, n, 1)
+        rho, u = W.taylor_green_2d(n, 0.05)
+        tau = W.taylor_green_2d_tau(n, 0.05)
+    with B.Solver(args.lattice, shape, tau, storage=storage) as s:
+        s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
+                      torch.from_numpy(u.astype(np.float32)).cuda())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.step(args.steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d = s.diagnostics()
+    cells = int(np.prod(shape))
+    print(f"lattice D{2 if args.lattice == 9 else 3}Q{args.lattice} {shape} {args.storage}: "
+          f"{args.steps} steps in {dt * 1e3:.2f} ms ({cells * args.steps / dt / 1e9:.2f} GLUPS), "
+          f"mass {d[0]:.6f}")
+
+
+if __name__ == "__main__":
+    main()
