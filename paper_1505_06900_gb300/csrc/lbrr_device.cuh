@@ -105,115 +105,119 @@ struct Macro {
   float pxx, pxy, pxz, pyy, pyz, pzz;
 };
 
-// Moments of a D2Q9 cell, separable sums over x then y.
-__device__ __forceinline__ Macro moments_d2q9(const float (&f)[9]) {
-  float s0[3], s1[3], s2[3];  // per y-line: sum, first and second x-moment
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    const float a = f[3 * l], b = f[3 * l + 1], c = f[3 * l + 2];
-    s2[l] = a + c;
-    s0[l] = s2[l] + b;
-    s1[l] = c - a;
-  }
+// One separable moment pass over a line of three values at xi = -1, 0, +1:
+// s0 = sum, s1 = first moment, s2 = second moment. With G (populations held
+// as g = df / w) the D1Q3 weights are applied as the integer ratios 1 : 4 : 1,
+// so every pass multiplies the moments by 6 (undone once at the end).
+template <bool G>
+__device__ __forceinline__ void mom3(float a, float b, float c, float &s0, float &s1, float &s2) {
+  s2 = a + c;
+  s0 = G ? fmaf(4.0f, b, s2) : s2 + b;
+  s1 = c - a;
+}
+
+// rho, rho u and Pi1 from the raw moments m000 (= rho - 1), first moments j
+// and second moments p_ab of df.
+__device__ __forceinline__ Macro macro_from_moments(float m0, float jx, float jy, float jz,
+                                                    float pxx, float pyy, float pzz, float pxy,
+                                                    float pxz, float pyz) {
   Macro m;
-  const float m00 = s0[0] + s0[1] + s0[2];
-  const float m01 = s0[2] - s0[0];
-  const float m02 = s0[2] + s0[0];
-  const float m10 = s1[0] + s1[1] + s1[2];
-  const float m11 = s1[2] - s1[0];
-  const float m20 = s2[0] + s2[1] + s2[2];
-  m.drho = m00;
-  m.rho = 1.0f + m00;
-  m.jx = m10;
-  m.jy = m01;
-  m.jz = 0.0f;
-  m.ux = m10 / m.rho;
-  m.uy = m01 / m.rho;
-  m.uz = 0.0f;
-  m.pxx = m20 - kCs2 * m00 - m10 * m.ux;
-  m.pxy = m11 - m10 * m.uy;
-  m.pyy = m02 - kCs2 * m00 - m01 * m.uy;
-  m.pxz = m.pyz = m.pzz = 0.0f;
+  m.drho = m0;
+  m.rho = 1.0f + m0;
+  m.jx = jx;
+  m.jy = jy;
+  m.jz = jz;
+  m.ux = jx / m.rho;
+  m.uy = jy / m.rho;
+  m.uz = jz / m.rho;
+  m.pxx = pxx - kCs2 * m0 - jx * m.ux;
+  m.pyy = pyy - kCs2 * m0 - jy * m.uy;
+  m.pzz = pzz - kCs2 * m0 - jz * m.uz;
+  m.pxy = pxy - jx * m.uy;
+  m.pxz = pxz - jx * m.uz;
+  m.pyz = pyz - jy * m.uz;
   return m;
 }
 
+// Moments of a D2Q9 cell, separable sums over x then y. G: inputs are g.
+template <bool G>
+__device__ __forceinline__ Macro moments_d2q9(const float (&f)[9]) {
+  float s0[3], s1[3], s2[3];  // per y-line: sum, first and second x-moment
+#pragma unroll
+  for (int l = 0; l < 3; ++l) mom3<G>(f[3 * l], f[3 * l + 1], f[3 * l + 2], s0[l], s1[l], s2[l]);
+  float m00, m01, m02, m10, m11, m12, m20, m21, m22;
+  mom3<G>(s0[0], s0[1], s0[2], m00, m01, m02);
+  mom3<G>(s1[0], s1[1], s1[2], m10, m11, m12);
+  mom3<G>(s2[0], s2[1], s2[2], m20, m21, m22);
+  const float k = G ? 1.0f / 36.0f : 1.0f;
+  return macro_from_moments(k * m00, k * m10, k * m01, 0.0f, k * m20, k * m02, 0.0f, k * m11,
+                            0.0f, 0.0f);
+}
+
 // Moments of a D3Q27 cell, separable sums over x, then y, then z.
+template <bool G>
 __device__ __forceinline__ Macro moments_d3q27(const float (&f)[27]) {
   float x0[9], x1[9], x2[9];
 #pragma unroll
-  for (int l = 0; l < 9; ++l) {
-    const float a = f[3 * l], b = f[3 * l + 1], c = f[3 * l + 2];
-    x2[l] = a + c;
-    x0[l] = x2[l] + b;
-    x1[l] = c - a;
-  }
+  for (int l = 0; l < 9; ++l) mom3<G>(f[3 * l], f[3 * l + 1], f[3 * l + 2], x0[l], x1[l], x2[l]);
   // y-pass per z-plane k: moments (x-power p, y-power q) with p + q <= 2
   float y00[3], y01[3], y02[3], y10[3], y11[3], y20[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int l = 3 * k;
-    y02[k] = x0[l] + x0[l + 2];
-    y00[k] = y02[k] + x0[l + 1];
-    y01[k] = x0[l + 2] - x0[l];
-    y10[k] = x1[l] + x1[l + 1] + x1[l + 2];
-    y11[k] = x1[l + 2] - x1[l];
-    y20[k] = x2[l] + x2[l + 1] + x2[l + 2];
+    float t0, t1, t2;
+    mom3<G>(x0[l], x0[l + 1], x0[l + 2], y00[k], y01[k], y02[k]);
+    mom3<G>(x1[l], x1[l + 1], x1[l + 2], y10[k], y11[k], t2);
+    mom3<G>(x2[l], x2[l + 1], x2[l + 2], y20[k], t1, t0);
   }
-  const float m000 = y00[0] + y00[1] + y00[2];
-  const float m001 = y00[2] - y00[0];
-  const float m002 = y00[2] + y00[0];
-  const float m010 = y01[0] + y01[1] + y01[2];
-  const float m011 = y01[2] - y01[0];
-  const float m020 = y02[0] + y02[1] + y02[2];
-  const float m100 = y10[0] + y10[1] + y10[2];
-  const float m101 = y10[2] - y10[0];
-  const float m110 = y11[0] + y11[1] + y11[2];
-  const float m200 = y20[0] + y20[1] + y20[2];
-  Macro m;
-  m.drho = m000;
-  m.rho = 1.0f + m000;
-  m.jx = m100;
-  m.jy = m010;
-  m.jz = m001;
-  m.ux = m100 / m.rho;
-  m.uy = m010 / m.rho;
-  m.uz = m001 / m.rho;
-  m.pxx = m200 - kCs2 * m000 - m100 * m.ux;
-  m.pyy = m020 - kCs2 * m000 - m010 * m.uy;
-  m.pzz = m002 - kCs2 * m000 - m001 * m.uz;
-  m.pxy = m110 - m100 * m.uy;
-  m.pxz = m101 - m100 * m.uz;
-  m.pyz = m011 - m010 * m.uz;
-  return m;
+  float m000, m001, m002, m010, m011, m020, m100, m101, m110, m200, t0, t1, t2, t3, t4, t5;
+  mom3<G>(y00[0], y00[1], y00[2], m000, m001, m002);
+  mom3<G>(y01[0], y01[1], y01[2], m010, m011, t0);
+  mom3<G>(y02[0], y02[1], y02[2], m020, t1, t2);
+  mom3<G>(y10[0], y10[1], y10[2], m100, m101, t3);
+  mom3<G>(y11[0], y11[1], y11[2], m110, t4, t5);
+  float t6, t7;
+  mom3<G>(y20[0], y20[1], y20[2], m200, t6, t7);
+  const float k = G ? 1.0f / 216.0f : 1.0f;
+  return macro_from_moments(k * m000, k * m100, k * m010, k * m001, k * m200, k * m020, k * m002,
+                            k * m110, k * m101, k * m011);
 }
 
 // ------------------------------------------------------------- synthesis --
-// 1-D synthesis T of coefficients (c0, c1, c2) at xi = -1, 0, +1.
+// 1-D synthesis T of coefficients (c0, c1, c2) at xi = -1, 0, +1; with G the
+// weight is divided out: T/w = (c0 - 3/2 c2, c0 +- 3 c1 + 3 c2).
+template <bool G>
 __device__ __forceinline__ void synth1(float c0, float c1, float c2, float &om, float &oz,
                                        float &op) {
-  const float q = fmaf(c0, kCs2, c2);
-  oz = c0 - q;
-  op = 0.5f * (q + c1);
-  om = 0.5f * (q - c1);
+  if (G) {
+    oz = fmaf(-1.5f, c2, c0);
+    const float p = fmaf(3.0f, c2, c0);
+    op = fmaf(3.0f, c1, p);
+    om = fmaf(-3.0f, c1, p);
+  } else {
+    const float q = fmaf(c0, kCs2, c2);
+    oz = c0 - q;
+    op = 0.5f * (q + c1);
+    om = 0.5f * (q - c1);
+  }
 }
 
-// Shifted post-collision populations of a D2Q9 cell (RR, Sec. 3.4):
-// df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1 rebuilds f0 + f1).
-// Coefficient of x^a y^b: C = px[a] Q1[b] + h[a] Q2[b] + dx[a] Q3[b] with
-// px = (1, ux, ux^2), h = (0, 0, 1), dx = (0, 1, 2 ux) (powers of ux and their
-// second and first ux-derivatives) and the y-vectors
+// Coefficients of the shifted post-collision populations of a D2Q9 cell
+// (RR, Sec. 3.4): df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1
+// rebuilds f0 + f1). Coefficient of x^a y^b: C = px[a] Q1[b] + h[a] Q2[b] +
+// dx[a] Q3[b] with px = (1, ux, ux^2), h = (0, 0, 1), dx = (0, 1, 2 ux) (powers
+// of ux and their second and first ux-derivatives) and the y-vectors
 //   Q1 = rho (1, uy, uy^2) + om1 Pi_yy (0, 0, 1)
 //   Q2 = om1 Pi_xx (1, uy, uy^2),   Q3 = om1 Pi_xy (0, 1, 2 uy).
 // The conserved coefficients are then set from the moments themselves
 // (C_00 = rho - 1, C_10 = rho ux, C_01 = rho uy), so that mass and momentum
 // pass through the update with no other rounding than the synthesis'.
-__device__ __forceinline__ void synth_rr_d2q9(const Macro &m, float om1, float (&f)[9]) {
+__device__ __forceinline__ void coeffs_rr_d2q9(const Macro &m, float om1, float (&c)[3][3]) {
   const float ux = m.ux, uy = m.uy, uyy = uy * uy;
   const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pxy = om1 * m.pxy;
   const float q1[3] = {m.rho, m.rho * uy, fmaf(m.rho, uyy, pyy)};
   const float q2[3] = {pxx, pxx * uy, pxx * uyy};
   const float q3[3] = {0.0f, pxy, 2.0f * pxy * uy};
-  float c[3][3];  // [a][b]
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
     c[0][b] = q1[b];
@@ -223,50 +227,73 @@ __device__ __forceinline__ void synth_rr_d2q9(const Macro &m, float om1, float (
   c[0][0] = m.drho;
   c[1][0] = m.jx;
   c[0][1] = m.jy;
+}
+
+// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
+// coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
+__device__ __forceinline__ void coeffs_reg2_d2q9(const Macro &m, float om1, float (&c)[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) c[a][b] = 0.0f;
+  c[0][0] = m.drho;
+  c[1][0] = m.jx;
+  c[0][1] = m.jy;
+  c[2][0] = fmaf(om1, m.pxx, m.jx * m.ux);
+  c[0][2] = fmaf(om1, m.pyy, m.jy * m.uy);
+  c[1][1] = fmaf(om1, m.pxy, m.jx * m.uy);
+}
+
+// Separable synthesis of a 3x3 coefficient matrix c[a][b] into the nine
+// populations, i = ix + 3 iy.
+template <bool G>
+__device__ __forceinline__ void synth_tensor_d2q9(const float (&c)[3][3], float (&f)[9]) {
   float s[3][3];  // [ix][b]
 #pragma unroll
-  for (int b = 0; b < 3; ++b) synth1(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
+  for (int b = 0; b < 3; ++b) synth1<G>(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
 #pragma unroll
-  for (int ix = 0; ix < 3; ++ix) synth1(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
+  for (int ix = 0; ix < 3; ++ix)
+    synth1<G>(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
 }
 
 // Separable synthesis of a 3x3x3 coefficient tensor c[a][b][c] (x, y, z
 // powers) into the 27 populations, i = ix + 3 iy + 9 iz.
+template <bool G>
 __device__ __forceinline__ void synth_tensor_d3q27(const float (&c)[3][3][3], float (&f)[27]) {
   float sx[3][3][3];  // [ix][b][c]
 #pragma unroll
   for (int b = 0; b < 3; ++b)
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc)
-      synth1(c[0][b][cc], c[1][b][cc], c[2][b][cc], sx[0][b][cc], sx[1][b][cc], sx[2][b][cc]);
+      synth1<G>(c[0][b][cc], c[1][b][cc], c[2][b][cc], sx[0][b][cc], sx[1][b][cc],
+                sx[2][b][cc]);
 #pragma unroll
   for (int ix = 0; ix < 3; ++ix) {
     float sy[3][3];  // [iy][c]
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc)
-      synth1(sx[ix][0][cc], sx[ix][1][cc], sx[ix][2][cc], sy[0][cc], sy[1][cc], sy[2][cc]);
+      synth1<G>(sx[ix][0][cc], sx[ix][1][cc], sx[ix][2][cc], sy[0][cc], sy[1][cc], sy[2][cc]);
 #pragma unroll
     for (int iy = 0; iy < 3; ++iy)
-      synth1(sy[iy][0], sy[iy][1], sy[iy][2], f[ix + 3 * iy], f[ix + 3 * iy + 9],
-             f[ix + 3 * iy + 18]);
+      synth1<G>(sy[iy][0], sy[iy][1], sy[iy][2], f[ix + 3 * iy], f[ix + 3 * iy + 9],
+                f[ix + 3 * iy + 18]);
   }
 }
 
-// Shifted post-collision populations of a D3Q27 cell (RR, Sec. 3.4). The
-// coefficient of x^a y^b z^c is C = px[a] Q1[b][c] + h[a] Q2[b][c] +
-// dx[a] Q3[b][c] (px, h, dx as in 2D) with the (y, z) matrices
+// Coefficients of the shifted post-collision populations of a D3Q27 cell
+// (RR, Sec. 3.4). The coefficient of x^a y^b z^c is C = px[a] Q1[b][c] +
+// h[a] Q2[b][c] + dx[a] Q3[b][c] (px, h, dx as in 2D) with the (y, z) matrices
 //   Q1 = rho py pz + om1 (Pi_yy h_y pz + Pi_zz py h_z + Pi_yz dy dz)
 //   Q2 = om1 Pi_xx py pz,   Q3 = om1 (Pi_xy dy pz + Pi_xz py dz),
 // i.e. f0's coefficients rho ux^a uy^b uz^c plus om1 times the recursion's
 // pair sums; the conserved coefficients come from the moments directly.
-__device__ __forceinline__ void synth_rr_d3q27(const Macro &m, float om1, float (&f)[27]) {
+__device__ __forceinline__ void coeffs_rr_d3q27(const Macro &m, float om1, float (&c)[3][3][3]) {
   const float ux = m.ux, uy = m.uy, uz = m.uz;
   const float py[3] = {1.0f, uy, uy * uy}, pz[3] = {1.0f, uz, uz * uz};
   const float dy[3] = {0.0f, 1.0f, 2.0f * uy}, dz[3] = {0.0f, 1.0f, 2.0f * uz};
   const float pxx = om1 * m.pxx, pyy = om1 * m.pyy, pzz = om1 * m.pzz;
   const float pxy = om1 * m.pxy, pxz = om1 * m.pxz, pyz = om1 * m.pyz;
   const float uxx = ux * ux, ux2 = 2.0f * ux;
-  float c[3][3][3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
 #pragma unroll
@@ -289,28 +316,16 @@ __device__ __forceinline__ void synth_rr_d3q27(const Macro &m, float om1, float 
   c[1][0][0] = m.jx;
   c[0][1][0] = m.jy;
   c[0][0][1] = m.jz;
-  synth_tensor_d3q27(c, f);
 }
 
-// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
-// coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
-__device__ __forceinline__ void synth_reg2_d2q9(const Macro &m, float om1, float (&f)[9]) {
-  float c[3][3] = {};  // [a][b] coefficient of x^a y^b
-  c[0][0] = m.drho;
-  c[1][0] = m.jx;
-  c[0][1] = m.jy;
-  c[2][0] = fmaf(om1, m.pxx, m.jx * m.ux);
-  c[0][2] = fmaf(om1, m.pyy, m.jy * m.uy);
-  c[1][1] = fmaf(om1, m.pxy, m.jx * m.uy);
-  float s[3][3];  // [ix][b]
+__device__ __forceinline__ void coeffs_reg2_d3q27(const Macro &m, float om1,
+                                                  float (&c)[3][3][3]) {
 #pragma unroll
-  for (int b = 0; b < 3; ++b) synth1(c[0][b], c[1][b], c[2][b], s[0][b], s[1][b], s[2][b]);
+  for (int a = 0; a < 3; ++a)
 #pragma unroll
-  for (int ix = 0; ix < 3; ++ix) synth1(s[ix][0], s[ix][1], s[ix][2], f[ix], f[ix + 3], f[ix + 6]);
-}
-
-__device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, float (&f)[27]) {
-  float c[3][3][3] = {};  // [a][b][c]
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) c[a][b][cc] = 0.0f;
   c[0][0][0] = m.drho;
   c[1][0][0] = m.jx;
   c[0][1][0] = m.jy;
@@ -321,35 +336,45 @@ __device__ __forceinline__ void synth_reg2_d3q27(const Macro &m, float om1, floa
   c[1][1][0] = fmaf(om1, m.pxy, m.jx * m.uy);
   c[1][0][1] = fmaf(om1, m.pxz, m.jx * m.uz);
   c[0][1][1] = fmaf(om1, m.pyz, m.jy * m.uz);
-  synth_tensor_d3q27(c, f);
 }
 
+// moments<G>(f): macroscopic moments of one cell (G: f holds g = df / w).
+// synth<MODEL, G>(m, om1, f): post-collision populations (MODEL 0: RR,
+// 1: order-2 regularized) as df, or as g with G.
 template <int Q>
 struct Lattice;
 template <>
 struct Lattice<9> {
   static constexpr int D = 2;
-  __device__ __forceinline__ static Macro moments(const float (&f)[9]) { return moments_d2q9(f); }
-  template <int MODEL>
+  template <bool G = false>
+  __device__ __forceinline__ static Macro moments(const float (&f)[9]) {
+    return moments_d2q9<G>(f);
+  }
+  template <int MODEL, bool G = false>
   __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[9]) {
+    float c[3][3];
     if (MODEL == 0)
-      synth_rr_d2q9(m, om1, f);
+      coeffs_rr_d2q9(m, om1, c);
     else
-      synth_reg2_d2q9(m, om1, f);
+      coeffs_reg2_d2q9(m, om1, c);
+    synth_tensor_d2q9<G>(c, f);
   }
 };
 template <>
 struct Lattice<27> {
   static constexpr int D = 3;
+  template <bool G = false>
   __device__ __forceinline__ static Macro moments(const float (&f)[27]) {
-    return moments_d3q27(f);
+    return moments_d3q27<G>(f);
   }
-  template <int MODEL>
+  template <int MODEL, bool G = false>
   __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[27]) {
+    float c[3][3][3];
     if (MODEL == 0)
-      synth_rr_d3q27(m, om1, f);
+      coeffs_rr_d3q27(m, om1, c);
     else
-      synth_reg2_d3q27(m, om1, f);
+      coeffs_reg2_d3q27(m, om1, c);
+    synth_tensor_d3q27<G>(c, f);
   }
 };
 

@@ -19,6 +19,12 @@ constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3,
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
                         int parity, cudaStream_t st);
 
+// The shared-memory tiled variant of launch_step for 16-bit stores
+// (lbrr_step16.cu); usable when tiled16_supported(g) (nx a multiple of 128).
+bool tiled16_supported(const Grid &g);
+cudaError_t launch_step_tiled16(int q, int storage, int model, void *f, const Grid &g, float om1,
+                                int parity, cudaStream_t st);
+
 // f = f0 + f1 (mode 1) or f0 (mode 0) from device fields rho [N], u [D][N].
 cudaError_t launch_init(int q, int storage, int model, void *f, const Grid &g, const float *rho,
                         const float *u, float tau, int mode, cudaStream_t st);

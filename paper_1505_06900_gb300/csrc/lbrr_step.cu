@@ -105,6 +105,8 @@ static cudaError_t step_s(int storage, int model, void *f, const Grid &g, float 
 
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
                         int parity, cudaStream_t st) {
+  if (storage != 0 && tiled16_supported(g))
+    return launch_step_tiled16(q, storage, model, f, g, om1, parity, st);
   return q == 9 ? step_s<9>(storage, model, f, g, om1, parity, st)
                 : step_s<27>(storage, model, f, g, om1, parity, st);
 }

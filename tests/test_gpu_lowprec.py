@@ -59,7 +59,10 @@ def raw_store(g: np.ndarray, storage: int, parity: int, c: np.ndarray) -> "torch
 
 @pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16])
 @pytest.mark.parametrize("parity", [0, 1])
-@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (260, 5, 1)), (O.D3Q27, (140, 5, 4))])
+# nx a multiple of 128 takes the shared-memory tiled kernel, other nx the
+# one-thread-per-cell kernel
+@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (260, 5, 1)), (O.D2Q9, (256, 3, 1)),
+                                           (O.D3Q27, (140, 5, 4)), (O.D3Q27, (256, 3, 4))])
 def test_one_update_is_correctly_rounded(storage, parity, lattice, shape):
     """Both AA kernels (the store is written at either parity from the host)."""
     _, q = O.dims_of(lattice)
