@@ -70,6 +70,7 @@ def _load():
                 "ora_fields": [i, i, i, i, i, dp, dp, dp, dp],
                 "ora_diagnostics": [i, i, i, i, dp, dp],
                 "ora_enstrophy": [i, i, i, i, dp, dp],
+                "ora_collide_cell_closure": [d, dp, dp, dp],
                 "ora_num_threads": [],
                 "ora_set_num_threads": [i],
             }
@@ -175,6 +176,19 @@ def collide_cell(lattice: int, f, tau: float, variant: int = RR) -> np.ndarray:
     ff = _f64(f)
     out = np.zeros(Q)
     _check(lib.ora_collide_cell(lattice, variant, float(tau), _dp(ff), _dp(out)), "collide_cell")
+    return out
+
+
+def collide_cell_closure(f, tau: float, delta) -> np.ndarray:
+    """D3Q27 collision with delta[17] added to the order 3..6 off-equilibrium
+    coefficients (the learned closure's correction)."""
+    lib = _load()
+    ff = _f64(f)
+    dd = _f64(delta)
+    assert ff.size == 27 and dd.size == 17
+    out = np.zeros(27)
+    _check(lib.ora_collide_cell_closure(float(tau), _dp(ff), _dp(dd), _dp(out)),
+           "collide_cell_closure")
     return out
 
 

@@ -432,6 +432,28 @@ int ora_collide_cell(int lattice, int variant, double tau, const double *f, doub
   return 0;
 }
 
+/* Post-collision populations of one D3Q27 cell with a learned correction
+ * delta[17] added to the recursion's off-equilibrium coefficients of orders
+ * 3..6 (in the order xxy, xxz, xyy, xzz, yzz, yyz, xyz, xxyy, xxzz, yyzz,
+ * xyzz, xyyz, xxyz, xxyzz, xxyyz, xyyzz, xxyyzz) before the (1 - 1/tau)
+ * relaxation of eq_discr_bgk_reg. delta = 0 is the RR collision. */
+int ora_collide_cell_closure(double tau, const double *f, const double *delta, double *out) {
+  ora_lattice L;
+  make_lattice(ORA_D3Q27, &L);
+  double rho, u[3];
+  hcoef a1;
+  density_velocity(&L, f, &rho, u);
+  neq_stress(&L, ORA_RR, f, rho, u, &a1);
+  recursive_coefficients(3, u, &a1);
+  double *hi[17] = {&a1.xxy,  &a1.xxz,  &a1.xyy,  &a1.xzz,   &a1.yzz,   &a1.yyz,
+                    &a1.xyz,  &a1.xxyy, &a1.xxzz, &a1.yyzz,  &a1.xyzz,  &a1.xyyz,
+                    &a1.xxyz, &a1.xxyzz, &a1.xxyyz, &a1.xyyzz, &a1.xxyyzz};
+  for (int k = 0; k < 17; ++k) *hi[k] += delta[k];
+  for (int i = 0; i < L.q; ++i)
+    out[i] = feq(&L, ORA_RR, i, rho, u) + (1.0 - 1.0 / tau) * fneq(&L, ORA_RR, i, &a1);
+  return 0;
+}
+
 /* nsteps full updates of eq_discr_bgk_reg on a periodic nx*ny*nz grid:
  * collide every cell, then pull-stream f_i(x) <- f_post_i(x - xi_i).
  * f is updated in place (a scratch array of the same size is allocated). */

@@ -1,0 +1,154 @@
+"""Pins of the FP64 learned-closure reference (oracle/closure.py) against
+library routines, finite differences, brute force and special cases."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import closure as C
+
+torch = pytest.importorskip("torch")
+
+
+def rand_params(rng, scale=0.2):
+    return C.unpack(scale * rng.standard_normal(C.N_PARAMS))
+
+
+def test_forward_matches_torch_float64():
+    rng = np.random.default_rng(0)
+    p = rand_params(rng)
+    X = rng.standard_normal((37, C.N_IN))
+    Y, _ = C.forward(X, p)
+    t = {k: torch.from_numpy(v) for k, v in p.items()}
+    h = torch.tanh(torch.nn.functional.linear(torch.from_numpy(X), t["W1"], t["b1"]))
+    h = torch.tanh(torch.nn.functional.linear(h, t["W2"], t["b2"]))
+    ref = torch.nn.functional.linear(h, t["W3"], t["b3"]).numpy()
+    assert np.abs(Y - ref).max() < 1e-13
+
+
+def test_backward_matches_central_differences():
+    rng = np.random.default_rng(1)
+    p = rand_params(rng, 0.3)
+    X = rng.standard_normal((9, C.N_IN))
+    T = rng.standard_normal((9, C.N_OUT))
+    Y, cache = C.forward(X, p)
+    g = C.backward(Y, T, cache, p)
+    flat, gflat = C.pack(p), C.pack(g)
+    idx = rng.choice(C.N_PARAMS, 60, replace=False)
+    # include biases and every layer
+    idx = np.concatenate([idx, [0, 18432, 18432 + 64, 22592 + 64, C.N_PARAMS - 1]])
+    h = 1e-5
+    for k in idx:
+        fp, fm = flat.copy(), flat.copy()
+        fp[k] += h
+        fm[k] -= h
+        lp = C.loss(C.forward(X, C.unpack(fp))[0], T)
+        lm = C.loss(C.forward(X, C.unpack(fm))[0], T)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[k]) <= 1e-6 * max(1e-3, abs(fd)), (k, fd, gflat[k])
+
+
+def test_loss_gradient_ignores_padded_outputs():
+    rng = np.random.default_rng(2)
+    p = rand_params(rng)
+    X = rng.standard_normal((5, C.N_IN))
+    T = rng.standard_normal((5, C.N_OUT))
+    Y, cache = C.forward(X, p)
+    g = C.backward(Y, T, cache, p)
+    assert np.all(g["W3"][C.N_OUT_USED:] == 0) and np.all(g["b3"][C.N_OUT_USED:] == 0)
+
+
+def test_adam_matches_torch():
+    rng = np.random.default_rng(3)
+    p = rand_params(rng)
+    tp = {k: torch.tensor(v, requires_grad=True) for k, v in p.items()}
+    opt = torch.optim.Adam(list(tp.values()), lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    state = {}
+    for _ in range(3):
+        g = {k: rng.standard_normal(v.shape) for k, v in p.items()}
+        p = C.adam(p, g, state, 1e-3)
+        for k, t in tp.items():
+            t.grad = torch.from_numpy(g[k])
+        opt.step()
+    for k in p:
+        assert np.abs(p[k] - tp[k].detach().numpy()).max() < 1e-14
+
+
+def test_bf16_round_matches_torch():
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(10000) * np.exp(rng.uniform(-20, 20, 10000))
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(C.bf16_round(x), ref)
+
+
+def test_coarsen_brute_force_and_mass():
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((27, 4, 6, 8))
+    cf = C.coarsen(f)
+    assert cf.shape == (27, 2, 3, 4)
+    for (i, z, y, x) in [(0, 0, 0, 0), (5, 1, 2, 3), (26, 1, 0, 2)]:
+        ref = np.mean([f[i, 2 * z + a, 2 * y + b, 2 * x + c]
+                       for a in (0, 1) for b in (0, 1) for c in (0, 1)])
+        assert abs(cf[i, z, y, x] - ref) < 1e-15
+    assert abs(cf.sum() * 8 - f.sum()) < 1e-11
+
+
+def test_features_brute_force():
+    rng = np.random.default_rng(6)
+    nx, ny, nz = 5, 4, 3
+    mom = rng.standard_normal((10, nz, ny, nx))
+    mean = rng.standard_normal(10)
+    inv = rng.uniform(0.5, 2.0, 10)
+    X = C.features(mom, mean, inv)
+    for (x, y, z) in [(0, 0, 0), (4, 3, 2), (2, 1, 1)]:
+        cell = (z * ny + y) * nx + x
+        for nb in range(27):
+            dx, dy, dz = nb % 3 - 1, (nb // 3) % 3 - 1, nb // 9 - 1
+            for k in range(10):
+                v = mom[k, (z + dz) % nz, (y + dy) % ny, (x + dx) % nx]
+                assert abs(X[cell, 10 * nb + k] - (v - mean[k]) * inv[k]) < 1e-14
+        assert np.all(X[cell, 270:] == 0)
+
+
+def test_targets_vanish_on_regularized_populations_and_rebuild_f():
+    c, w = O.lattice_tables(O.D3Q27)
+    rng = np.random.default_rng(7)
+    shape = (3, 2, 2)
+    f = w[:, None, None, None] * (1 + 0.1 * rng.standard_normal((27, 2, 2, 3)))
+    # the regularized populations (tau -> infinity) have no residual
+    freg = np.stack([O.collide_cell(O.D3Q27, f[:, z, y, x], 1e15)
+                     for z in range(2) for y in range(2) for x in range(3)], axis=1)
+    freg = freg.reshape(27, 2, 2, 3)
+    assert np.abs(C.targets(freg)).max() < 1e-13
+    # f = f_RR + sum over the 17 members of w pref_k H_k delta_k
+    H, pref = O.hermite_basis(O.D3Q27)
+    d = C.targets(f)
+    fr = f.reshape(27, -1)
+    frr = freg.reshape(27, -1)
+    rebuilt = frr + (w[:, None] * (H[10:27].T * pref[10:27]) @ d.T)
+    assert np.abs(rebuilt - fr).max() < 1e-14
+
+
+def test_closure_collision_special_cases():
+    c, w = O.lattice_tables(O.D3Q27)
+    H, _ = O.hermite_basis(O.D3Q27)
+    rng = np.random.default_rng(8)
+    f = w * (1 + 0.1 * rng.standard_normal(27))
+    tau = 0.8
+    rr = O.collide_cell(O.D3Q27, f, tau)
+    assert np.array_equal(O.collide_cell_closure(f, tau, np.zeros(17)), rr)
+    delta = 1e-3 * rng.standard_normal(17)
+    post = O.collide_cell_closure(f, tau, delta)
+    # orders 0..2 untouched, orders 3..6 shifted by (1 - 1/tau) delta
+    assert np.abs(H[:10] @ (post - rr)).max() < 1e-16
+    assert np.abs(H[10:] @ (post - rr) - (1 - 1 / tau) * delta).max() < 1e-16
+
+
+def test_step_closure_with_zero_network_is_rr():
+    from paper_1505_06900_gb300 import workloads as W
+    shape = (4, 4, 4)
+    rho, u = W.random_field(shape, 3, seed=9)
+    tau = 0.7
+    f = O.init(O.D3Q27, shape, tau, rho, u)
+    p = C.unpack(np.zeros(C.N_PARAMS))
+    got = C.step_closure(f, tau, p, np.zeros(10), np.ones(10), np.ones(17))
+    assert np.abs(got - O.step(O.D3Q27, shape, tau, f, 1)).max() < 1e-16
