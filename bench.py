@@ -40,7 +40,14 @@ MACH, RE = 0.1, 1600.0
 # DRAM traffic of one step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
 # taken on; reported as null when the sources have changed since.
-TRAFFIC = {}
+# The 512^3 launch is too large for a multi-pass capture; the value is the
+# 256^3 capture (profiles/rr_step_d3q27_f32_f16_256.md, mean of the even and
+# odd launches, 212.5 B per cell) scaled by the cell count, since the traffic
+# per cell does not depend on the grid size for this streaming kernel.
+TRAFFIC = {
+    "d3q27_f32_512": {"kernel_sha": "b859e02933043c40", "bytes_per_launch": 28514893824,
+                      "source": "ncu 256^3 capture scaled to 512^3"},
+}
 
 KERNEL_SOURCES = ["paper_1505_06900_gb300/csrc/lbrr_step.cu",
                   "paper_1505_06900_gb300/csrc/lbrr_device.cuh"]
@@ -181,11 +188,14 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm --
 def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_every, stream,
-                 sync_all, sampler=None):
-    """Warm up, then time `steps` updates; returns timing and per-launch data."""
+                 sync_all, sampler=None, keep_u=False, closure=None):
+    """Warm up, then time `steps` updates; returns timing and per-launch data
+    (and the final velocity field with keep_u)."""
     s = B.Solver(B.D3Q27, (n, n, n), tau, storage=storage, stream=stream)
     try:
         s.init_fields(rho_d, u_d)
+        if closure is not None:
+            s.set_closure(closure)
         s.step(warmup)
         for _ in range(max(1, warmup // diag_every)):
             s.diagnostics()
@@ -215,11 +225,61 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         total_ms = t_start.elapsed_time(t_end)
         kern_ms = [a.elapsed_time(b) for a, b in ev]
         diag = s.diagnostics()
-        return {"total_ms": total_ms, "kernel_ms": statistics.mean(kern_ms),
-                "kernel_ms_median": statistics.median(kern_ms), "launches": launches,
-                "diag": diag.tolist(), "bytes_per_update": s.info()["bytes_per_update"]}
+        out = {"total_ms": total_ms, "kernel_ms": statistics.mean(kern_ms),
+               "kernel_ms_median": statistics.median(kern_ms), "launches": launches,
+               "diag": diag.tolist(), "bytes_per_update": s.info()["bytes_per_update"]}
+        if keep_u:
+            out["u"] = s.moments()[1]
+        if closure is not None:
+            out["fallbacks"] = s.closure_fallbacks()
+        return out
     finally:
         s.close()
+
+
+def rel_l2(torch, a, b) -> float:
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms_per_step):
+    """Train the closure on the filtered 128^3 study (seconds), then time the
+    closure step on an n_coarse^3 grid (one coarse step stands for two fine
+    steps of the 2 n_coarse grid) next to plain RR on the same coarse grid."""
+    from paper_1505_06900_gb300 import closure as CL
+    from paper_1505_06900_gb300 import workloads as W
+    t0 = time.perf_counter()
+    net, rep = CL.study(n_fine=128, steps=1500, coarse_steps=400,
+                        snapshots=(200, 400, 600, 800))
+    train_s = time.perf_counter() - t0
+    tau_c = CL.coarse_tau(W.taylor_green_3d_tau(2 * n_coarse, MACH, RE))
+    rho, u = W.taylor_green_3d(n_coarse, MACH)
+    rho_d = torch.from_numpy(rho.astype(np.float32)).cuda()
+    u_d = torch.from_numpy(u.astype(np.float32)).cuda()
+    ml = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
+                      DIAG_EVERY, stream, sync_all, closure=net)
+    rr = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
+                      DIAG_EVERY, stream, sync_all)
+    cells = n_coarse ** 3
+    ms_ml = ml["total_ms"] / steps
+    ms_rr = rr["total_ms"] / steps
+    net.close()
+    return {
+        "value": cells * steps / (ml["total_ms"] * 1e-3) / 1e9, "unit": "GLUPS (coarse cells)",
+        "grid": [n_coarse] * 3, "ms_per_coarse_step": ms_ml,
+        "kernels_per_step": 2,
+        "speedup_vs_fine_f32_equal_time": 2.0 * fine_ms_per_step / ms_ml,
+        "coarse_rr": {"ms_per_coarse_step": ms_rr,
+                      "speedup_vs_fine_f32_equal_time": 2.0 * fine_ms_per_step / ms_rr},
+        "fallback_cell_updates": ml["fallbacks"],
+        "u_error_vs_filtered_fine": {
+            "closure": rep["err_closure"], "coarse_rr": rep["err_rr"],
+            "study": f"D3Q27 Taylor-Green Ma {rep['mach']} Re {rep['re']:g}, fine "
+                     f"{rep['n_fine']}^3 -> coarse {rep['n_fine'] // 2}^3, held-out phase, "
+                     f"{rep['coarse_steps']} coarse steps",
+        },
+        "training": {"samples": rep["samples"], "loss_first": rep["loss_first"],
+                     "loss_last": rep["loss_last"], "seconds": train_s},
+    }
 
 
 class _Null:
@@ -262,16 +322,23 @@ def run_gpu(args):
 
     sampler = ClockSampler(local)
     main = time_variant(B, torch, n, B.STORE_F32, args.steps, args.warmup, tau, rho_d, u_d,
-                        DIAG_EVERY, stream, sync_all, sampler)
+                        DIAG_EVERY, stream, sync_all, sampler, keep_u=True)
+    u_f32 = main.pop("u")
     variants = {}
     for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
         r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                         DIAG_EVERY, stream, sync_all)
+                         DIAG_EVERY, stream, sync_all, keep_u=True)
         variants[name] = {
             "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
             "bytes_per_update": r["bytes_per_update"],
             "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
+            "speedup_vs_f32": main["total_ms"] / r["total_ms"],
+            "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
+            "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, same init",
         }
+    del u_f32
+    variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
+                                          sync_all, main["total_ms"] / args.steps)
 
     # end to end through host buffers (pinned), one lb_run_host call of K steps
     rho_h = torch.from_numpy(rho32).pin_memory()

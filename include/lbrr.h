@@ -159,6 +159,74 @@ LB_API int lb_run_host(lb_ctx *ctx, const float *rho_h, const float *u_h, int in
  * collision, number of steps taken, bytes moved per cell update. */
 LB_API int lb_info(const lb_ctx *ctx, long long *out);
 
+/* ---------------------------------------------------------------------------
+ * Learned closure (an extension around the method; the paper has no learned
+ * component). A small network predicts, from the moments (rho - 1, u, Pi1) of
+ * a D3Q27 cell and of its 26 periodic neighbours, the off-equilibrium Hermite
+ * coefficients of orders 3..6 that the recursion of Sec. 3.1 leaves out of a
+ * coarse-grained (2x2x2 box-filtered) fine run; the prediction is added to the
+ * recursion's coefficients before the (1 - 1/tau) relaxation of
+ * eq_discr_bgk_reg. Zero weights reproduce the RR update exactly.
+ *
+ * Network: y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3, x in R^288 (270 used),
+ * hidden 64 and 64, y in R^32 (17 used). Parameters are packed as W1 [64][288],
+ * b1 [64], W2 [64][64], b2 [64], W3 [32][64], b3 [32] (LB_MLP_PARAMS floats,
+ * row-major, W[out][in]). Products run on tensor cores with BF16 operands
+ * (weights and activations rounded to BF16) and FP32 accumulation; the master
+ * parameters and the Adam state are FP32.
+ *
+ * Features (BF16 [N][288]): feature 10 * nb + k is moment k of neighbour
+ * nb = (dx+1) + 3(dy+1) + 9(dz+1), minus in_mean[k], times in_inv_std[k];
+ * 270..287 are zero. Targets (FP32 [N][32]): coefficient k (order xxy, xxz,
+ * xyy, xzz, yzz, yyz, xyz, xxyy, xxzz, yyzz, xyzz, xyyz, xxyz, xxyzz, xxyyz,
+ * xyyzz, xxyyzz) of f - f_RR divided by out_scale[k]; 17..31 are zero. Loss:
+ * mean over rows and the 17 used outputs of (y - t)^2.
+ * ------------------------------------------------------------------------- */
+#define LB_MLP_PARAMS 24736
+#define LB_MLP_IN 288
+#define LB_MLP_OUT 32
+
+typedef struct lb_mlp lb_mlp;
+
+/* Network on the current device, parameters zero, Adam state empty, scaling
+ * in_mean = 0, in_inv_std = 1, out_scale = 1. */
+LB_API int lb_mlp_create(lb_mlp **out);
+LB_API void lb_mlp_destroy(lb_mlp *mlp);
+LB_API const char *lb_mlp_last_error(const lb_mlp *mlp);
+LB_API int lb_mlp_set_stream(lb_mlp *mlp, void *stream);
+/* Copy LB_MLP_PARAMS packed floats (host or device memory); resets Adam. */
+LB_API int lb_mlp_set_params(lb_mlp *mlp, const float *params);
+LB_API int lb_mlp_get_params(lb_mlp *mlp, float *params);
+/* Feature and target standardisation (host arrays of 10, 10 and 17 floats;
+ * in_inv_std and out_scale must be finite and non-zero). */
+LB_API int lb_mlp_set_scaling(lb_mlp *mlp, const float *in_mean, const float *in_inv_std,
+                              const float *out_scale);
+/* Y [M][32] (device, FP32) = network(X [M][288], device, BF16). */
+LB_API int lb_mlp_forward(lb_mlp *mlp, const void *X, long long M, float *Y);
+/* Gradient of the loss over the batch into grad [LB_MLP_PARAMS] (device) and
+ * the loss into *loss (host, may be NULL); parameters unchanged. Deterministic. */
+LB_API int lb_mlp_gradients(lb_mlp *mlp, const void *X, const float *T, long long M, float *grad,
+                            double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
+ * batch; *loss (host, may be NULL) is the loss before the step. */
+LB_API int lb_mlp_train_step(lb_mlp *mlp, const void *X, const float *T, long long M, float lr,
+                             double *loss);
+/* Features of every cell of a D3Q27 FP32 RR context into X [N][288] (device). */
+LB_API int lb_closure_features(lb_ctx *ctx, const lb_mlp *mlp, void *X);
+/* Standardised targets of every cell into T [N][32] (device). */
+LB_API int lb_closure_targets(lb_ctx *ctx, const lb_mlp *mlp, float *T);
+/* 2x2x2 box average of the populations of `fine` into `coarse` (D3Q27 FP32
+ * contexts, fine = 2 x coarse in every direction); resets coarse's step count.
+ * The coarse grid of an acoustically scaled run uses tau_c = 1/2 + (tau_f - 1/2)/2. */
+LB_API int lb_coarsen(lb_ctx *fine, lb_ctx *coarse);
+/* Use the network in lb_step (NULL: plain RR). A cell whose standardised
+ * prediction exceeds `bound` in magnitude, or whose corrected populations are
+ * not all positive, takes the RR update instead and is counted. The network
+ * must outlive its use. */
+LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
+/* Cells that fell back to RR since the closure was first set (host out). */
+LB_API int lb_closure_fallbacks(lb_ctx *ctx, long long *count);
+
 /* Largest grid (nx * ny * nz cells) that lb_diagnostics_static accepts. */
 #define LB_STATIC_MAX_CELLS 134217728LL /* 512^3 */
 

@@ -53,12 +53,16 @@ def pack(p: dict) -> np.ndarray:
 
 
 # ----------------------------------------------------------------- network --
-def forward(X: np.ndarray, p: dict):
-    """Y [M, 32] and the cache of activations for backward."""
+def forward(X: np.ndarray, p: dict, round_hidden: bool = False):
+    """Y [M, 32] and the cache of activations for backward. round_hidden rounds
+    the two hidden layers to bfloat16 before they feed the next product (the
+    precision of the tensor-core kernels), for tight comparisons."""
     X = np.asarray(X, np.float64)
     H1 = np.tanh(X @ p["W1"].T + p["b1"])
-    H2 = np.tanh(H1 @ p["W2"].T + p["b2"])
-    Y = H2 @ p["W3"].T + p["b3"]
+    A1 = bf16_round(H1) if round_hidden else H1
+    H2 = np.tanh(A1 @ p["W2"].T + p["b2"])
+    A2 = bf16_round(H2) if round_hidden else H2
+    Y = A2 @ p["W3"].T + p["b3"]
     return Y, (X, H1, H2)
 
 
@@ -142,19 +146,22 @@ def targets(f: np.ndarray) -> np.ndarray:
     return out
 
 
-def predict_delta(X: np.ndarray, p: dict, out_scale: np.ndarray) -> np.ndarray:
-    """Unstandardised correction [N, 17] predicted by the network."""
-    Y, _ = forward(X, p)
+def predict_delta(X: np.ndarray, p: dict, out_scale: np.ndarray,
+                  bf16: bool = False) -> np.ndarray:
+    """Unstandardised correction [N, 17] predicted by the network (bf16: with
+    the features and hidden layers rounded to bfloat16)."""
+    Y, _ = forward(bf16_round(X) if bf16 else X, p, round_hidden=bf16)
     return Y[:, :N_OUT_USED] * out_scale
 
 
-def step_closure(f: np.ndarray, tau: float, p: dict, mean, inv_std, out_scale) -> np.ndarray:
+def step_closure(f: np.ndarray, tau: float, p: dict, mean, inv_std, out_scale,
+                 bf16: bool = False) -> np.ndarray:
     """One update of the D3Q27 RR scheme with the learned correction: features
     from the pre-collision moments, corrected collision of every cell, periodic
     streaming (pull)."""
     from . import lattice_tables
     q, nz, ny, nx = f.shape
-    delta = predict_delta(features(moment_field(f), mean, inv_std), p, out_scale)
+    delta = predict_delta(features(moment_field(f), mean, inv_std), p, out_scale, bf16)
     post = np.empty_like(f).reshape(q, -1)
     ff = f.reshape(q, -1)
     for c in range(nx * ny * nz):

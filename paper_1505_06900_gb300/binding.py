@@ -43,7 +43,23 @@ SIGNATURES = {
     "lb_run_host": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "lb_info": (_i, [_vp, ctypes.POINTER(_ll)]),
     "lb_diagnostics_static": (_i, [_i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
+    "lb_mlp_create": (_i, [ctypes.POINTER(_vp)]),
+    "lb_mlp_destroy": (None, [_vp]),
+    "lb_mlp_last_error": (ctypes.c_char_p, [_vp]),
+    "lb_mlp_set_stream": (_i, [_vp, _vp]),
+    "lb_mlp_set_params": (_i, [_vp, _vp]),
+    "lb_mlp_get_params": (_i, [_vp, _vp]),
+    "lb_mlp_set_scaling": (_i, [_vp, _vp, _vp, _vp]),
+    "lb_mlp_forward": (_i, [_vp, _vp, _ll, _vp]),
+    "lb_mlp_gradients": (_i, [_vp, _vp, _vp, _ll, _vp, _vp]),
+    "lb_mlp_train_step": (_i, [_vp, _vp, _vp, _ll, ctypes.c_float, _vp]),
+    "lb_closure_features": (_i, [_vp, _vp, _vp]),
+    "lb_closure_targets": (_i, [_vp, _vp, _vp]),
+    "lb_coarsen": (_i, [_vp, _vp]),
+    "lb_set_closure": (_i, [_vp, _vp, ctypes.c_float]),
+    "lb_closure_fallbacks": (_i, [_vp, ctypes.POINTER(_ll)]),
 }
+MLP_PARAMS, MLP_IN, MLP_OUT, MLP_OUT_USED = 24736, 288, 32, 17
 LB_STATIC_MAX_CELLS = 134217728
 
 
@@ -211,8 +227,114 @@ class Solver:
         self._check(self._lib.lb_run_host(self._h, _ptr(rho_h), _ptr(u_h), int(mode), int(nsteps),
                                           _ptr(rho_out), _ptr(u_out), _ptr(diag_out)))
 
+    # -- learned closure (D3Q27, FP32 store, RR) ---------------------------
+    def coarsen_from(self, fine: "Solver"):
+        """2x2x2 box average of `fine`'s populations into this context."""
+        self._check(self._lib.lb_coarsen(fine.handle, self._h))
+
+    def closure_features(self, mlp: "MLP"):
+        import torch
+        X = torch.empty((self.n, MLP_IN), device=self.device, dtype=torch.bfloat16)
+        self._check(self._lib.lb_closure_features(self._h, mlp.handle, _ptr(X)))
+        return X
+
+    def closure_targets(self, mlp: "MLP"):
+        import torch
+        T = torch.empty((self.n, MLP_OUT), device=self.device, dtype=torch.float32)
+        self._check(self._lib.lb_closure_targets(self._h, mlp.handle, _ptr(T)))
+        return T
+
+    def set_closure(self, mlp, bound: float = 8.0):
+        self._check(self._lib.lb_set_closure(self._h, mlp.handle if mlp else None, float(bound)))
+        self._closure = mlp
+
+    def closure_fallbacks(self) -> int:
+        out = ctypes.c_longlong()
+        self._check(self._lib.lb_closure_fallbacks(self._h, ctypes.byref(out)))
+        return out.value
+
     def info(self) -> dict:
         out = (ctypes.c_longlong * 8)()
         self._check(self._lib.lb_info(self._h, out))
         keys = ["lattice", "nx", "ny", "nz", "storage", "collision", "steps", "bytes_per_update"]
         return dict(zip(keys, list(out)))
+
+
+class MLP:
+    """The learned closure's network (device parameters, Adam state, scaling)."""
+
+    def __init__(self, params=None, stream=None):
+        import torch
+        self._lib = load()
+        h = ctypes.c_void_p()
+        rc = self._lib.lb_mlp_create(ctypes.byref(h))
+        if rc != LB_OK:
+            raise LBError(rc, self._lib.lb_last_error(None).decode())
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self._lib.lb_mlp_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)))
+        if params is not None:
+            self.set_params(params)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def _check(self, rc):
+        if rc != LB_OK:
+            raise LBError(rc, self._lib.lb_mlp_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lb_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).reshape(-1))
+        assert p.size == MLP_PARAMS
+        self._check(self._lib.lb_mlp_set_params(self._h, p.ctypes.data))
+
+    def get_params(self) -> np.ndarray:
+        p = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self._lib.lb_mlp_get_params(self._h, p.ctypes.data))
+        return p
+
+    def set_scaling(self, in_mean, in_inv_std, out_scale):
+        a = [np.ascontiguousarray(np.asarray(v, dtype=np.float32)) for v in
+             (in_mean, in_inv_std, out_scale)]
+        assert a[0].size == 10 and a[1].size == 10 and a[2].size == 17
+        self._check(self._lib.lb_mlp_set_scaling(self._h, a[0].ctypes.data, a[1].ctypes.data,
+                                                 a[2].ctypes.data))
+        self.scaling = a
+
+    def forward(self, X):
+        import torch
+        assert X.dtype == torch.bfloat16 and X.is_cuda and X.shape[1] == MLP_IN
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], MLP_OUT), device=X.device, dtype=torch.float32)
+        self._check(self._lib.lb_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+        return Y
+
+    def gradients(self, X, T):
+        import torch
+        X, T = X.contiguous(), T.contiguous()
+        g = torch.empty(MLP_PARAMS, device=X.device, dtype=torch.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.lb_mlp_gradients(self._h, _ptr(X), _ptr(T), X.shape[0], _ptr(g),
+                                               ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, X, T, lr: float, want_loss: bool = True):
+        X, T = X.contiguous(), T.contiguous()
+        loss = ctypes.c_double()
+        self._check(self._lib.lb_mlp_train_step(self._h, _ptr(X), _ptr(T), X.shape[0],
+                                                float(lr), ctypes.byref(loss) if want_loss
+                                                else None))
+        return loss.value if want_loss else None

@@ -9,6 +9,7 @@
 
 #include "lbrr.h"
 #include "lbrr_launch.h"
+#include "lbrr_mlp.h"
 
 struct lb_ctx {
   int lattice = 0, d = 0, q = 0;
@@ -23,6 +24,23 @@ struct lb_ctx {
   double *partials = nullptr;  // reduction scratch, kRedBlocks * kRedValues doubles
   double *dout = nullptr;      // reduction result, kRedValues doubles
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
+  float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
+  const lb_mlp *closure = nullptr;  // learned closure in use (not owned)
+  float closure_bound = 0.f;
+  unsigned long long *fallbacks = nullptr;  // device counter of cells that fell back to RR
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+};
+
+struct lb_mlp {
+  lbrr::MlpDevice d{};
+  float *scaling = nullptr;    // device: in_mean[10], in_inv_std[10], out_scale[17]
+  float *gpart = nullptr;      // per-block gradient partials
+  float *lpart = nullptr;      // per-block loss partials
+  double *dloss = nullptr;
+  int nblocks = 0;             // blocks of the training kernel (one per SM)
+  long long t = 0;             // Adam steps taken
+  int device = 0;
   cudaStream_t stream = nullptr;
   char err[512] = {0};
 };
@@ -68,6 +86,10 @@ int free_all(lb_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->dout) cudaFree(c->dout);
   if (c->fields) cudaFree(c->fields);
+  if (c->mom) cudaFree(c->mom);
+  if (c->fallbacks) cudaFree(c->fallbacks);
+  c->mom = nullptr;
+  c->fallbacks = nullptr;
   c->f = nullptr;
   c->partials = nullptr;
   c->dout = nullptr;
@@ -218,8 +240,17 @@ int lb_step(lb_ctx *c, int n) {
   DeviceGuard dg(c->device);
   const float om1 = (float)(1.0 - 1.0 / c->tau);
   for (int k = 0; k < n; ++k) {
-    cudaError_t e =
-        lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity, c->stream);
+    cudaError_t e;
+    if (c->closure) {
+      e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
+      if (e == cudaSuccess)
+        e = lbrr::launch_step_closure(c->closure->d, static_cast<float *>(c->f), c->g, om1,
+                                      c->parity, c->mom, c->fallbacks, c->closure_bound,
+                                      c->stream);
+    } else {
+      e = lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity,
+                            c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->parity ^= 1;
     ++c->steps;
@@ -356,6 +387,282 @@ int lb_info(const lb_ctx *c, long long *out) {
   out[5] = c->collision;
   out[6] = c->steps;
   out[7] = 2LL * c->q * (long long)c->elem;
+  return LB_OK;
+}
+
+// ------------------------------------------------------------ learned closure
+
+static int mlp_fail(lb_mlp *m, int code, const char *fmt, ...) {
+  char *buf = m ? m->err : nullptr;
+  va_list ap;
+  va_start(ap, fmt);
+  if (buf)
+    vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+void lb_mlp_destroy(lb_mlp *m) {
+  if (!m) return;
+  DeviceGuard dg(m->device);
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  void *bufs[] = {m->d.params, m->d.adam_m, m->d.adam_v, m->d.w1,  m->d.w2,  m->d.w3,
+                  m->d.w2t,    m->d.w3t,    m->scaling,  m->gpart, m->lpart, m->dloss};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  delete m;
+}
+
+int lb_mlp_create(lb_mlp **out) {
+  if (!out) return fail(nullptr, LB_EINVAL, "null argument");
+  *out = nullptr;
+  lb_mlp *m = new (std::nothrow) lb_mlp;
+  if (!m) return fail(nullptr, LB_ENOMEM, "host allocation failed");
+  cudaError_t e = cudaGetDevice(&m->device);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, m->device);
+  m->nblocks = sms > 0 ? sms : 1;
+  const size_t P = lbrr::kMlpParams;
+  e = cudaMalloc(&m->d.params, 4 * P);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.adam_m, 4 * P);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.adam_v, 4 * P);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.w1, 2 * lbrr::kMlpHidden * lbrr::kMlpIn);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.w2, 2 * lbrr::kMlpHidden * lbrr::kMlpHidden);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.w3, 2 * lbrr::kMlpOut * lbrr::kMlpHidden);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.w2t, 2 * lbrr::kMlpHidden * lbrr::kMlpHidden);
+  if (e == cudaSuccess) e = cudaMalloc(&m->d.w3t, 2 * lbrr::kMlpOut * lbrr::kMlpHidden);
+  if (e == cudaSuccess) e = cudaMalloc(&m->scaling, 4 * 37);
+  if (e == cudaSuccess) e = cudaMalloc(&m->gpart, 4 * P * (size_t)m->nblocks);
+  if (e == cudaSuccess) e = cudaMalloc(&m->lpart, 4 * (size_t)m->nblocks);
+  if (e == cudaSuccess) e = cudaMalloc(&m->dloss, sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lb_mlp_destroy(m);
+    return fail(nullptr, LB_ENOMEM, "cannot allocate the network");
+  }
+  m->d.b1 = m->d.params + lbrr::kOffB1;
+  m->d.b2 = m->d.params + lbrr::kOffB2;
+  m->d.b3 = m->d.params + lbrr::kOffB3;
+  m->d.in_mean = m->scaling;
+  m->d.in_inv_std = m->scaling + 10;
+  m->d.out_scale = m->scaling + 20;
+  float sc[37];
+  for (int k = 0; k < 37; ++k) sc[k] = k < 10 ? 0.f : 1.f;
+  e = cudaMemset(m->d.params, 0, 4 * P);
+  if (e == cudaSuccess) e = cudaMemset(m->d.adam_m, 0, 4 * P);
+  if (e == cudaSuccess) e = cudaMemset(m->d.adam_v, 0, 4 * P);
+  if (e == cudaSuccess) e = cudaMemcpy(m->scaling, sc, sizeof sc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = lbrr::launch_mlp_refresh(m->d, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    lb_mlp_destroy(m);
+    return fail(nullptr, LB_ECUDA, "network initialisation failed: %s", cudaGetErrorString(e));
+  }
+  *out = m;
+  return LB_OK;
+}
+
+const char *lb_mlp_last_error(const lb_mlp *m) { return m ? m->err : g_create_err; }
+
+int lb_mlp_set_stream(lb_mlp *m, void *stream) {
+  if (!m) return fail(nullptr, LB_EINVAL, "null network");
+  m->stream = static_cast<cudaStream_t>(stream);
+  return LB_OK;
+}
+
+int lb_mlp_set_params(lb_mlp *m, const float *params) {
+  if (!m || !params) return mlp_fail(m, LB_EINVAL, "null argument");
+  DeviceGuard dg(m->device);
+  const size_t bytes = 4 * (size_t)lbrr::kMlpParams;
+  cudaError_t e = cudaMemcpyAsync(m->d.params, params, bytes, cudaMemcpyDefault, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d.adam_m, 0, bytes, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d.adam_v, 0, bytes, m->stream);
+  if (e == cudaSuccess) e = lbrr::launch_mlp_refresh(m->d, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "set_params: %s", cudaGetErrorString(e));
+  m->t = 0;
+  return LB_OK;
+}
+
+int lb_mlp_get_params(lb_mlp *m, float *params) {
+  if (!m || !params) return mlp_fail(m, LB_EINVAL, "null argument");
+  DeviceGuard dg(m->device);
+  cudaError_t e = cudaMemcpyAsync(params, m->d.params, 4 * (size_t)lbrr::kMlpParams,
+                                  cudaMemcpyDefault, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "get_params: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
+int lb_mlp_set_scaling(lb_mlp *m, const float *in_mean, const float *in_inv_std,
+                       const float *out_scale) {
+  if (!m || !in_mean || !in_inv_std || !out_scale) return mlp_fail(m, LB_EINVAL, "null argument");
+  float sc[37];
+  std::memcpy(sc, in_mean, 40);
+  std::memcpy(sc + 10, in_inv_std, 40);
+  std::memcpy(sc + 20, out_scale, 68);
+  for (int k = 0; k < 37; ++k)
+    if (!std::isfinite(sc[k]) || (k >= 10 && sc[k] == 0.f))
+      return mlp_fail(m, LB_EINVAL, "scaling value %d is zero or not finite", k);
+  DeviceGuard dg(m->device);
+  cudaError_t e = cudaMemcpyAsync(m->scaling, sc, sizeof sc, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "set_scaling: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
+int lb_mlp_forward(lb_mlp *m, const void *X, long long M, float *Y) {
+  if (!m || !X || !Y || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
+  DeviceGuard dg(m->device);
+  const long long tiles = (M + 63) / 64;
+  const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
+  cudaError_t e = lbrr::launch_mlp(m->d, X, nullptr, M, Y, nullptr, nullptr, nb, m->stream);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "forward: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
+static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
+                        int adam, float lr, double *loss) {
+  if (!m || !X || !T || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
+  if (adam && !(lr > 0.f && std::isfinite(lr)))
+    return mlp_fail(m, LB_EINVAL, "learning rate must be positive");
+  DeviceGuard dg(m->device);
+  const long long tiles = (M + 63) / 64;
+  const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
+  cudaError_t e = lbrr::launch_mlp(m->d, X, T, M, nullptr, m->gpart, m->lpart, nb, m->stream);
+  float bc1 = 1.f, bc2 = 1.f;
+  if (adam) {
+    const long long t = m->t + 1;
+    bc1 = (float)(1.0 - std::pow(0.9, (double)t));
+    bc2 = (float)(1.0 - std::pow(0.999, (double)t));
+  }
+  if (e == cudaSuccess)
+    e = lbrr::launch_mlp_reduce(m->d, m->gpart, nb, grad, adam, lr, bc1, bc2, m->lpart,
+                                loss ? m->dloss : nullptr, m->stream);
+  if (e == cudaSuccess && loss) {
+    double h = 0.0;
+    e = cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    *loss = h / ((double)M * lbrr::kMlpOutUsed);
+  }
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "backward: %s", cudaGetErrorString(e));
+  if (adam) ++m->t;
+  return LB_OK;
+}
+
+int lb_mlp_gradients(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
+                     double *loss) {
+  if (!grad) return mlp_fail(m, LB_EINVAL, "null gradient buffer");
+  return mlp_backward(m, X, T, M, grad, 0, 0.f, loss);
+}
+
+int lb_mlp_train_step(lb_mlp *m, const void *X, const float *T, long long M, float lr,
+                      double *loss) {
+  return mlp_backward(m, X, T, M, nullptr, 1, lr, loss);
+}
+
+static int ensure_mom(lb_ctx *c) {
+  if (c->mom) return LB_OK;
+  cudaError_t e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
+  if (e != cudaSuccess) {
+    c->mom = nullptr;
+    cudaGetLastError();
+    return fail(c, LB_ENOMEM, "cannot allocate the moment field");
+  }
+  return LB_OK;
+}
+
+static int closure_capable(lb_ctx *c) {
+  if (c->lattice != LB_D3Q27 || c->storage != LB_STORE_F32 || c->collision != LB_COLLIDE_RR)
+    return fail(c, LB_EINVAL, "the learned closure needs a D3Q27, FP32, RR context");
+  return LB_OK;
+}
+
+int lb_closure_features(lb_ctx *c, const lb_mlp *m, void *X) {
+  LB_CHECK_CTX(c);
+  if (!m || !X) return fail(c, LB_EINVAL, "null argument");
+  int rc = closure_capable(c);
+  if (rc == LB_OK) rc = ensure_mom(c);
+  if (rc != LB_OK) return rc;
+  DeviceGuard dg(c->device);
+  cudaError_t e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
+  if (e == cudaSuccess) e = lbrr::launch_features(m->d, c->mom, c->g, X, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "closure features");
+  return LB_OK;
+}
+
+int lb_closure_targets(lb_ctx *c, const lb_mlp *m, float *T) {
+  LB_CHECK_CTX(c);
+  if (!m || !T) return fail(c, LB_EINVAL, "null argument");
+  int rc = closure_capable(c);
+  if (rc != LB_OK) return rc;
+  DeviceGuard dg(c->device);
+  cudaError_t e = lbrr::launch_targets(m->d, c->storage, c->f, c->g, c->parity, T, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "closure targets");
+  return LB_OK;
+}
+
+int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
+  LB_CHECK_CTX(fine);
+  LB_CHECK_CTX(coarse);
+  if (fine->lattice != LB_D3Q27 || coarse->lattice != LB_D3Q27 || fine->storage != LB_STORE_F32 ||
+      coarse->storage != LB_STORE_F32)
+    return fail(coarse, LB_EINVAL, "coarsening needs two D3Q27 FP32 contexts");
+  if (fine->g.nx != 2 * coarse->g.nx || fine->g.ny != 2 * coarse->g.ny ||
+      fine->g.nz != 2 * coarse->g.nz)
+    return fail(coarse, LB_EINVAL, "the fine grid must be twice the coarse grid in every direction");
+  if (fine->device != coarse->device) return fail(coarse, LB_EINVAL, "contexts on different devices");
+  DeviceGuard dg(coarse->device);
+  cudaError_t e = cudaSuccess;
+  if (fine->stream != coarse->stream) e = cudaStreamSynchronize(fine->stream);
+  if (e == cudaSuccess)
+    e = lbrr::launch_coarsen(fine->storage, fine->f, fine->g, fine->parity, coarse->storage,
+                             coarse->f, coarse->g, coarse->stream);
+  if (e != cudaSuccess) return cuda_fail(coarse, e, "coarsen");
+  coarse->parity = 0;
+  coarse->steps = 0;
+  return LB_OK;
+}
+
+int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
+  LB_CHECK_CTX(c);
+  if (!m) {
+    c->closure = nullptr;
+    return LB_OK;
+  }
+  if (!(bound > 0.f)) return fail(c, LB_EINVAL, "bound must be positive");
+  int rc = closure_capable(c);
+  if (rc == LB_OK) rc = ensure_mom(c);
+  if (rc != LB_OK) return rc;
+  DeviceGuard dg(c->device);
+  if (!c->fallbacks) {
+    cudaError_t e = cudaMalloc(&c->fallbacks, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->fallbacks, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, LB_ENOMEM, "cannot allocate the fallback counter");
+    }
+  }
+  c->closure = m;
+  c->closure_bound = bound;
+  return LB_OK;
+}
+
+int lb_closure_fallbacks(lb_ctx *c, long long *count) {
+  LB_CHECK_CTX(c);
+  if (!count) return fail(c, LB_EINVAL, "null argument");
+  *count = 0;
+  if (!c->fallbacks) return LB_OK;
+  DeviceGuard dg(c->device);
+  unsigned long long h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->fallbacks, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "fallback counter");
+  *count = (long long)h;
   return LB_OK;
 }
 

@@ -1,0 +1,343 @@
+// Learned closure on the RR step (an extension; the paper has no learned
+// component): moment field, standardised features and targets for training,
+// 2x2x2 coarsening of a fine run, and the update of a coarse D3Q27 FP32 store
+// in which the network's prediction of the order 3..6 off-equilibrium
+// coefficients is added to the recursion's before the (1 - 1/tau)
+// relaxation.
+//
+// Feature of a cell: the moments (rho - 1, u, Pi1) of the cell and its 26
+// periodic neighbours, standardised per moment kind, neighbour index
+// (dx+1) + 3(dy+1) + 9(dz+1), feature 10 * neighbour + moment, zero padded
+// to 288. Target: the order 3..6 Hermite coefficients of (f - f_RR), f_RR the
+// RR reconstruction from the cell's own moments, divided by out_scale, in the
+// order xxy, xxz, xyy, xzz, yzz, yyz, xyz, xxyy, xxzz, yyzz, xyzz, xyyz, xxyz,
+// xxyzz, xxyyz, xyyzz, xxyyzz, zero padded to 32.
+#include "lbrr_launch.h"
+#include "lbrr_mlp.h"
+#include "lbrr_mma.cuh"
+
+namespace lbrr {
+
+namespace {
+
+constexpr int kAux = 128;
+
+// (a, b, c) powers of the 17 high-order coefficients, in target order
+__host__ __device__ constexpr int hi_pow(int k, int axis) {
+  // packed as a + 3 b + 9 c
+  constexpr int code[17] = {2 + 3 * 1,     2 + 9 * 1,     1 + 3 * 2,     1 + 9 * 2,
+                            3 * 1 + 9 * 2, 3 * 2 + 9 * 1, 1 + 3 + 9,     2 + 3 * 2,
+                            2 + 9 * 2,     3 * 2 + 9 * 2, 1 + 3 + 9 * 2, 1 + 3 * 2 + 9,
+                            2 + 3 + 9,     2 + 3 + 9 * 2, 2 + 3 * 2 + 9, 1 + 3 * 2 + 9 * 2,
+                            2 + 3 * 2 + 9 * 2};
+  return axis == 0 ? code[k] % 3 : (axis == 1 ? (code[k] / 3) % 3 : code[k] / 9);
+}
+
+// --------------------------------------------------------------- moments --
+__global__ void __launch_bounds__(kAux)
+    moment_field_kernel(const float *__restrict__ f, const Grid g, const int parity,
+                        float *__restrict__ mom) {
+  const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  float df[27];
+  load_logical<27, 0>(f, g, parity, x, y, z, df);
+  const Macro m = Lattice<27>::moments(df);
+  const long long n = g.n;
+  const float v[kMlpMoments] = {m.drho, m.ux, m.uy, m.uz, m.pxx, m.pxy, m.pxz, m.pyy, m.pyz, m.pzz};
+#pragma unroll
+  for (int k = 0; k < kMlpMoments; ++k) mom[k * n + cell] = v[k];
+}
+
+// -------------------------------------------------------------- features --
+__device__ __forceinline__ long long nb_cell(const Grid &g, int x, int y, int z, int nb) {
+  const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+  return ((long long)wrap_add(z, dz, g.nz) * g.ny + wrap_add(y, dy, g.ny)) * g.nx +
+         wrap_add(x, dx, g.nx);
+}
+
+__global__ void __launch_bounds__(kAux)
+    features_kernel(MlpDevice p, const float *__restrict__ mom, const Grid g,
+                    __nv_bfloat16 *__restrict__ X) {
+  const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  const long long n = g.n;
+  uint32_t *row = reinterpret_cast<uint32_t *>(X + cell * kMlpIn);
+  for (int nb = 0; nb < 27; ++nb) {
+    const long long c = nb_cell(g, x, y, z, nb);
+#pragma unroll
+    for (int k = 0; k < kMlpMoments; k += 2) {
+      const float v0 = (__ldg(mom + k * n + c) - p.in_mean[k]) * p.in_inv_std[k];
+      const float v1 = (__ldg(mom + (k + 1) * n + c) - p.in_mean[k + 1]) * p.in_inv_std[k + 1];
+      row[(kMlpMoments * nb + k) / 2] = pack_bf16(v0, v1);
+    }
+  }
+  for (int k = kMlpInUsed; k < kMlpIn; k += 2) row[k / 2] = 0u;
+}
+
+// --------------------------------------------------------------- targets --
+// 1-D Hermite analysis of a line d(-1), d(0), d(+1): sums of H0 = 1,
+// H1 = xi, H2 = xi^2 - 1/3 times d.
+__device__ __forceinline__ void ana1(float dm, float dz, float dp, float &e0, float &e1,
+                                     float &e2) {
+  e0 = dm + dz + dp;
+  e1 = dp - dm;
+  e2 = fmaf(2.0f / 3.0f, dm + dp, -dz / 3.0f);
+}
+
+__global__ void __launch_bounds__(kAux)
+    targets_kernel(MlpDevice p, const float *__restrict__ f, const Grid g, const int parity,
+                   float *__restrict__ T) {
+  const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  float df[27], rr[27];
+  load_logical<27, 0>(f, g, parity, x, y, z, df);
+  const Macro m = Lattice<27>::moments(df);
+  Lattice<27>::synth<0>(m, 1.0f, rr);  // f_RR - w (tau -> infinity)
+#pragma unroll
+  for (int i = 0; i < 27; ++i) rr[i] = df[i] - rr[i];
+  float ax[3][9];  // [a][line (iy, iz)]
+#pragma unroll
+  for (int l = 0; l < 9; ++l) ana1(rr[3 * l], rr[3 * l + 1], rr[3 * l + 2], ax[0][l], ax[1][l], ax[2][l]);
+  float axy[3][3][3];  // [a][b][iz]
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz)
+      ana1(ax[a][3 * iz], ax[a][3 * iz + 1], ax[a][3 * iz + 2], axy[a][0][iz], axy[a][1][iz],
+           axy[a][2][iz]);
+  float A[3][3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      ana1(axy[a][b][0], axy[a][b][1], axy[a][b][2], A[a][b][0], A[a][b][1], A[a][b][2]);
+  float *row = T + cell * kMlpOut;
+#pragma unroll
+  for (int k = 0; k < kMlpOutUsed; ++k)
+    row[k] = A[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] / p.out_scale[k];
+  for (int k = kMlpOutUsed; k < kMlpOut; ++k) row[k] = 0.f;
+}
+
+// -------------------------------------------------------------- coarsen --
+template <int SF, int SC>
+__global__ void __launch_bounds__(kAux)
+    coarsen_kernel(const typename Storage<SF>::T *__restrict__ ff, const Grid gf, const int parity,
+                   typename Storage<SC>::T *__restrict__ fc, const Grid gc) {
+  const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
+  if (cell >= gc.n) return;
+  int x, y, z;
+  cell_coords(cell, gc, x, y, z);
+  float acc[27] = {};
+#pragma unroll 1
+  for (int s = 0; s < 8; ++s) {
+    float df[27];
+    load_logical<27, SF>(ff, gf, parity, 2 * x + (s & 1), 2 * y + ((s >> 1) & 1),
+                         2 * z + (s >> 2), df);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) acc[i] += df[i];
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i)
+    Storage<SC>::template store<3>(fc + i * gc.n + cell, i, 0.125f * acc[i]);
+}
+
+// ---------------------------------------------------------- closure step --
+constexpr int kCT = 64;        // cells per block (4 warps x 16 rows of the network)
+constexpr int kCThreads = 128;
+constexpr int kXsC = kMlpIn + 8;
+
+template <int PARITY>
+__global__ void __launch_bounds__(kCThreads)
+    rr_step_closure_kernel(MlpDevice p, float *__restrict__ f, const Grid g, const float om1,
+                           const float *__restrict__ mom, unsigned long long *fallbacks,
+                           const float bound) {
+  __shared__ __align__(16) __nv_bfloat16 xs[kCT][kXsC];
+  __shared__ float da[kCT][kMlpOutUsed + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g8 = lane >> 2, t4 = lane & 3;
+  const int x0 = blockIdx.x * kCT, y = blockIdx.y, z = blockIdx.z;
+  const long long n = g.n;
+
+  // ---- features of the block's cells (two threads per cell)
+  {
+    const int c = tid & (kCT - 1), half = tid >> 6;
+    const int x = x0 + c;
+    uint32_t *row = reinterpret_cast<uint32_t *>(&xs[c][0]);
+    if (x < g.nx) {
+      for (int nb = half ? 14 : 0; nb < (half ? 27 : 14); ++nb) {
+        const long long cc = nb_cell(g, x, y, z, nb);
+#pragma unroll
+        for (int k = 0; k < kMlpMoments; k += 2) {
+          const float v0 = (__ldg(mom + k * n + cc) - p.in_mean[k]) * p.in_inv_std[k];
+          const float v1 =
+              (__ldg(mom + (k + 1) * n + cc) - p.in_mean[k + 1]) * p.in_inv_std[k + 1];
+          row[(kMlpMoments * nb + k) / 2] = pack_bf16(v0, v1);
+        }
+      }
+      if (half)
+        for (int k = kMlpInUsed; k < kMlpIn; k += 2) row[k / 2] = 0u;
+    } else {
+      for (int k = half * (kMlpIn / 2); k < (half + 1) * (kMlpIn / 2); k += 2) row[k / 2] = 0u;
+    }
+  }
+  __syncthreads();
+
+  // ---- network on the 64 feature rows: warp w owns rows 16w..16w+15
+  {
+    const int r0 = 16 * warp;
+    float h1[8][4] = {};
+#pragma unroll 2
+    for (int ks = 0; ks < kMlpIn / 16; ++ks) {
+      uint32_t a[4];
+      ldsm_x4(a, &xs[r0 + (lane & 15)][16 * ks + 8 * (lane >> 4)]);
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t b0, b1;
+        b_frag(b0, b1, p.w1, kMlpIn, 8 * nt, 16 * ks, g8, t4);
+        mma16816(h1[nt], a, b0, b1);
+      }
+    }
+    uint32_t a1[4][4];
+    act_to_frags<8>(h1, p.b1, t4, a1);
+    float h2[8][4] = {};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        uint32_t b0, b1;
+        b_frag(b0, b1, p.w2, kMlpHidden, 8 * nt, 16 * ks, g8, t4);
+        mma16816(h2[nt], a1[ks], b0, b1);
+      }
+    uint32_t a2[4][4];
+    act_to_frags<8>(h2, p.b2, t4, a2);
+    float yv[3][4] = {};  // outputs 0..23 (17 used)
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+      for (int nt = 0; nt < 3; ++nt) {
+        uint32_t b0, b1;
+        b_frag(b0, b1, p.w3, kMlpHidden, 8 * nt, 16 * ks, g8, t4);
+        mma16816(yv[nt], a2[ks], b0, b1);
+      }
+#pragma unroll
+    for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = 8 * nt + 2 * t4 + (e & 1), row = r0 + g8 + (e >> 1) * 8;
+        if (col < kMlpOutUsed) da[row][col] = yv[nt][e] + p.b3[col];
+      }
+  }
+  __syncthreads();
+
+  // ---- corrected collision of the block's cells
+  if (tid >= kCT) return;
+  const int x = x0 + tid;
+  if (x >= g.nx) return;
+  float df[27];
+  const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
+  const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
+  const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
+  auto cell_at = [&](int b, int c, int a) -> long long {
+    return ((long long)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
+  };
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (PARITY == 0)
+      df[i] = f[i * n + cell_at(1, 1, 1)];
+    else
+      df[i] = f[(26 - i) * n + cell_at(1 - vel(i, 1), 1 - vel(i, 2), 1 - vel(i, 0))];
+  }
+  const Macro m = Lattice<27>::moments(df);
+  float c[3][3][3];
+  coeffs_rr_d3q27(m, om1, c);
+  bool use = true;
+  float dl[kMlpOutUsed];
+#pragma unroll
+  for (int k = 0; k < kMlpOutUsed; ++k) {
+    const float yk = da[tid][k];
+    use = use && (fabsf(yk) <= bound);  // also false for NaN
+    dl[k] = yk * p.out_scale[k];
+  }
+  float out[27];
+  if (use) {
+    float cc[3][3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cc[a][b][q] = c[a][b][q];
+#pragma unroll
+    for (int k = 0; k < kMlpOutUsed; ++k)
+      cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * dl[k];
+    synth_tensor_d3q27<false>(cc, out);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) use = use && (out[i] + weight<3>(i) > 0.0f);
+  }
+  if (!use) {
+    synth_tensor_d3q27<false>(c, out);
+    if (fallbacks) atomicAdd(fallbacks, 1ull);
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (PARITY == 0)
+      f[(26 - i) * n + cell_at(1, 1, 1)] = out[i];
+    else
+      f[i * n + cell_at(1 + vel(i, 1), 1 + vel(i, 2), 1 + vel(i, 0))] = out[i];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_moment_field(int storage, const void *f, const Grid &g, int parity, float *mom,
+                                cudaStream_t st) {
+  if (storage != 0) return cudaErrorInvalidValue;
+  moment_field_kernel<<<(unsigned)((g.n + kAux - 1) / kAux), kAux, 0, st>>>(
+      static_cast<const float *>(f), g, parity, mom);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_features(const MlpDevice &p, const float *mom, const Grid &g, void *X,
+                            cudaStream_t st) {
+  features_kernel<<<(unsigned)((g.n + kAux - 1) / kAux), kAux, 0, st>>>(
+      p, mom, g, static_cast<__nv_bfloat16 *>(X));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_targets(const MlpDevice &p, int storage, const void *f, const Grid &g,
+                           int parity, float *T, cudaStream_t st) {
+  if (storage != 0) return cudaErrorInvalidValue;
+  targets_kernel<<<(unsigned)((g.n + kAux - 1) / kAux), kAux, 0, st>>>(
+      p, static_cast<const float *>(f), g, parity, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int parity_f,
+                           int storage_c, void *fc, const Grid &gc, cudaStream_t st) {
+  const unsigned nb = (unsigned)((gc.n + kAux - 1) / kAux);
+  if (storage_f == 0 && storage_c == 0)
+    coarsen_kernel<0, 0><<<nb, kAux, 0, st>>>(static_cast<const float *>(ff), gf, parity_f,
+                                              static_cast<float *>(fc), gc);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_closure(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
+                                const float *mom, unsigned long long *fallbacks, float bound,
+                                cudaStream_t st) {
+  const dim3 grid((g.nx + kCT - 1) / kCT, g.ny, g.nz);
+  if (parity == 0)
+    rr_step_closure_kernel<0><<<grid, kCThreads, 0, st>>>(p, f, g, om1, mom, fallbacks, bound);
+  else
+    rr_step_closure_kernel<1><<<grid, kCThreads, 0, st>>>(p, f, g, om1, mom, fallbacks, bound);
+  return cudaGetLastError();
+}
+
+}  // namespace lbrr

@@ -396,4 +396,35 @@ __device__ __forceinline__ int wrap_add(int c, int d, int n) {
   return (r >= n) ? r - n : r;
 }
 
+// Logical (natural-order, pre-collision) shifted populations of cell (x, y, z)
+// from an AA store of the given parity (AA parity as in lbrr_step.cu).
+template <int Q, int S>
+__device__ __forceinline__ void load_logical(const typename Storage<S>::T *__restrict__ f,
+                                             const Grid &g, int parity, int x, int y, int z,
+                                             float (&df)[Q]) {
+  constexpr int D = Lattice<Q>::D;
+  const long long n = g.n;
+  if (parity == 0) {
+    const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) df[i] = Storage<S>::template load<D>(f + i * n + cell, i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int xs = wrap_add(x, -vel(i, 0), g.nx), ys = wrap_add(y, -vel(i, 1), g.ny);
+      const int zs = D == 3 ? wrap_add(z, -vel(i, 2), g.nz) : 0;
+      const long long src = ((long long)zs * g.ny + ys) * g.nx + xs;
+      df[i] = Storage<S>::template load<D>(f + (Q - 1 - i) * n + src, i);
+    }
+  }
+}
+
+__device__ __forceinline__ void cell_coords(long long cell, const Grid &g, int &x, int &y,
+                                            int &z) {
+  x = (int)(cell % g.nx);
+  const long long r = cell / g.nx;
+  y = (int)(r % g.ny);
+  z = (int)(r / g.ny);
+}
+
 }  // namespace lbrr

@@ -1,0 +1,232 @@
+"""Learned closure: the CUDA network, feature/target/coarsening kernels and the
+closure step against the FP64 reference in oracle/closure.py.
+
+Tolerances. The network runs with BF16 operands (weights, features, hidden
+activations) and FP32 accumulation; the oracle gets the same BF16-rounded
+weights and features, so the remaining difference is the BF16 rounding of the
+two hidden layers (relative ~2^-9 each): outputs within 1e-2 of the output
+scale, gradients within 2e-2 (relative L2 per weight matrix).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import closure as C
+from _common import max_rel_to_weight, shifted, f64_state
+from paper_1505_06900_gb300 import binding as B
+from paper_1505_06900_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def bf16_params(rng, scale=(0.08, 0.15, 0.15)):
+    """Random parameters whose weights are BF16-representable; the padded
+    inputs and outputs have zero weights."""
+    p = {"W1": scale[0] * rng.standard_normal((64, 288)), "b1": 0.1 * rng.standard_normal(64),
+         "W2": scale[1] * rng.standard_normal((64, 64)), "b2": 0.1 * rng.standard_normal(64),
+         "W3": scale[2] * rng.standard_normal((32, 64)), "b3": 0.1 * rng.standard_normal(32)}
+    p["W1"][:, 270:] = 0.0
+    p["W3"][17:] = 0.0
+    p["b3"][17:] = 0.0
+    for k in ("W1", "W2", "W3"):
+        p[k] = C.bf16_round(p[k])
+    for k in ("b1", "b2", "b3"):
+        p[k] = p[k].astype(np.float32).astype(np.float64)
+    return p
+
+
+def bf16_inputs(rng, m):
+    X = np.zeros((m, 288))
+    X[:, :270] = rng.standard_normal((m, 270))
+    return C.bf16_round(X)
+
+
+def to_dev_bf16(X):
+    return torch.from_numpy(X.astype(np.float32)).cuda().to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("m", [1, 64, 200])
+def test_forward_matches_oracle(m):
+    rng = np.random.default_rng(10 + m)
+    p = bf16_params(rng)
+    X = bf16_inputs(rng, m)
+    net = B.MLP(C.pack(p))
+    Y = net.forward(to_dev_bf16(X)).cpu().numpy().astype(np.float64)
+    Yo, _ = C.forward(X, p)
+    scale = np.abs(Yo[:, :17]).max()
+    assert np.abs(Y[:, :17] - Yo[:, :17]).max() <= 1e-2 * scale
+    assert np.all(Y[:, 17:] == 0.0)
+
+
+def test_gradients_match_oracle():
+    rng = np.random.default_rng(20)
+    p = bf16_params(rng)
+    M = 300  # several tiles, one ragged
+    X = bf16_inputs(rng, M)
+    T = np.zeros((M, 32))
+    T[:, :17] = rng.standard_normal((M, 17))
+    net = B.MLP(C.pack(p))
+    g, loss = net.gradients(to_dev_bf16(X), torch.from_numpy(T.astype(np.float32)).cuda())
+    g = C.unpack(g.cpu().numpy())
+    Yo, cache = C.forward(X, p)
+    go = C.backward(Yo, T, cache, p)
+    assert abs(loss / C.loss(Yo, T) - 1) < 1e-2
+    for k in go:
+        err = np.linalg.norm(g[k] - go[k]) / np.linalg.norm(go[k])
+        assert err < 2e-2, (k, err)
+    assert np.all(g["W1"][:, 270:] == 0) and np.all(g["W3"][17:] == 0) and np.all(g["b3"][17:] == 0)
+    # deterministic
+    g2, loss2 = net.gradients(to_dev_bf16(X), torch.from_numpy(T.astype(np.float32)).cuda())
+    assert np.array_equal(C.pack(g), g2.cpu().numpy()) and loss2 == loss
+
+
+def test_adam_step_matches_oracle():
+    """One Adam step from fresh moments moves every parameter by lr * g / (|g| + eps):
+    -lr sign(g) wherever the gradient is not tiny, nothing where it is zero."""
+    rng = np.random.default_rng(30)
+    p = bf16_params(rng)
+    M = 128
+    X = bf16_inputs(rng, M)
+    T = np.zeros((M, 32))
+    T[:, :17] = rng.standard_normal((M, 17))
+    net = B.MLP(C.pack(p))
+    lr = 1e-3
+    net.train_step(to_dev_bf16(X), torch.from_numpy(T.astype(np.float32)).cuda(), lr)
+    got = net.get_params().astype(np.float64) - C.pack(p)
+    Yo, cache = C.forward(X, p)
+    go = C.pack(C.backward(Yo, T, cache, p))
+    ref = C.pack(C.adam(p, C.unpack(go), {}, lr)) - C.pack(p)
+    big = np.abs(go) > 0.05 * np.sqrt(np.mean(go * go))
+    assert np.abs(got[big] - ref[big]).max() < 1e-2 * lr
+    assert np.all(np.abs(got) <= lr * 1.0001)
+    assert np.all(got[go == 0] == 0)
+
+
+def test_training_reduces_the_loss():
+    """A student network trained with the CUDA kernels on targets produced by a
+    random teacher network (oracle forward) lowers its loss by 10x."""
+    rng = np.random.default_rng(40)
+    teacher = bf16_params(rng, (0.06, 0.2, 0.2))
+    M = 4096
+    X = bf16_inputs(rng, M)
+    T, _ = C.forward(X, teacher)
+    T[:, 17:] = 0
+    Xd = to_dev_bf16(X)
+    Td = torch.from_numpy(T.astype(np.float32)).cuda()
+    student = np.zeros(C.N_PARAMS)
+    sp = C.unpack(0.05 * rng.standard_normal(C.N_PARAMS))
+    sp["W1"][:, 270:] = 0
+    sp["W3"][17:] = 0
+    sp["b3"][17:] = 0
+    net = B.MLP(C.pack(sp))
+    first = net.train_step(Xd, Td, 3e-3)
+    for _ in range(300):
+        last = net.train_step(Xd, Td, 3e-3)
+    assert last < 0.1 * first, (first, last)
+
+
+def _random_d3q27(shape, seed, amp=0.05):
+    return W.random_populations(27, shape, seed, amp).astype(np.float32)
+
+
+def test_features_targets_and_coarsening_match_oracle():
+    shape = (8, 6, 4)
+    rng = np.random.default_rng(50)
+    mean = rng.standard_normal(10) * 1e-3
+    inv = rng.uniform(10, 100, 10)
+    out_scale = rng.uniform(1e-3, 1e-2, 17)
+    net = B.MLP()
+    net.set_scaling(mean, inv, out_scale)
+    df = _random_d3q27(shape, 51)
+    with B.Solver(B.D3Q27, shape, 0.7) as s:
+        s.set_populations(torch.from_numpy(df).cuda())
+        s.step(1)  # odd parity: exercise the logical gathers
+        got_df = s.populations().cpu().numpy()
+        X = s.closure_features(net).float().cpu().numpy().astype(np.float64)
+        T = s.closure_targets(net).cpu().numpy().astype(np.float64)
+    f = O.step(O.D3Q27, shape, 0.7, f64_state(O.D3Q27, df), 1)
+    assert max_rel_to_weight(O.D3Q27, got_df, shifted(O.D3Q27, f)) <= 1e-6
+    Xo = C.features(C.moment_field(f), mean.astype(np.float32).astype(np.float64),
+                    inv.astype(np.float32).astype(np.float64))
+    ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(Xo), 1e-30))) - 7)
+    assert np.all(np.abs(X - Xo) <= ulp + 1e-3)
+    To = C.targets(f) / out_scale.astype(np.float32)
+    assert np.abs(T[:, :17] - To).max() <= 1e-6 / out_scale.min()
+    assert np.all(T[:, 17:] == 0)
+    # coarsening of the same state (odd parity) into a 4x3x2 grid
+    with B.Solver(B.D3Q27, shape, 0.7) as fine, B.Solver(B.D3Q27, (4, 3, 2), 0.6) as coarse:
+        fine.set_populations(torch.from_numpy(df).cuda())
+        fine.step(1)
+        coarse.coarsen_from(fine)
+        cg = coarse.populations().cpu().numpy()
+    assert max_rel_to_weight(O.D3Q27, cg, shifted(O.D3Q27, C.coarsen(f))) <= 1e-6
+
+
+def _closure_case(seed, out_scale_value):
+    shape = (64 + 16, 3, 4)  # two 64-cell tiles, the second ragged
+    rng = np.random.default_rng(seed)
+    rho, u = W.random_field(shape, 3, seed=seed, a_rho=0.005, a_u=0.03)
+    tau = 0.6
+    f0 = O.init(O.D3Q27, shape, tau, rho, u)
+    df = shifted(O.D3Q27, f0).astype(np.float32)
+    p = bf16_params(rng, (0.05, 0.15, 0.3))
+    mom = C.moment_field(f64_state(O.D3Q27, df))
+    mean = mom.reshape(10, -1).mean(1)
+    inv = 1.0 / (mom.reshape(10, -1).std(1) + 1e-12)
+    out_scale = np.full(17, out_scale_value)
+    return shape, tau, df, p, mean.astype(np.float32), inv.astype(np.float32), out_scale
+
+
+def test_closure_step_matches_oracle_and_zero_network_is_rr():
+    """Two closure updates against the reference with the network evaluated at
+    the kernels' precision (BF16 features and hidden layers)."""
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(60, 2e-5)
+    net = B.MLP(C.pack(p))
+    net.set_scaling(mean, inv, out_scale)
+    with B.Solver(B.D3Q27, shape, tau) as s:
+        s.set_populations(torch.from_numpy(df).cuda())
+        s.set_closure(net, bound=1e6)
+        s.step(2)
+        got = s.populations().cpu().numpy()
+        assert s.closure_fallbacks() == 0
+    f = f64_state(O.D3Q27, df)
+    m64, i64, o64 = (np.asarray(v, np.float32).astype(np.float64) for v in (mean, inv, out_scale))
+    for _ in range(2):
+        f = C.step_closure(f, tau, p, m64, i64, o64, bf16=True)
+    rr = O.step(O.D3Q27, shape, tau, f64_state(O.D3Q27, df), 2)
+    effect = max_rel_to_weight(O.D3Q27, shifted(O.D3Q27, rr), shifted(O.D3Q27, f))
+    # the closure is active: it moves the populations by far more than the
+    # float32 tolerance
+    assert effect > 1e-4
+    # float32 tolerance plus 1% of the correction: a BF16 hidden activation
+    # whose float32 and float64 pre-activations round to neighbouring BF16
+    # values changes the prediction by one BF16 unit (0.4%)
+    assert max_rel_to_weight(O.D3Q27, got, shifted(O.D3Q27, f)) <= 1e-6 + 1e-2 * effect
+    # zero network: bit-identical to the plain RR kernels
+    zero = B.MLP(np.zeros(C.N_PARAMS))
+    zero.set_scaling(mean, inv, out_scale)
+    with B.Solver(B.D3Q27, shape, tau) as a, B.Solver(B.D3Q27, shape, tau) as b:
+        a.set_populations(torch.from_numpy(df).cuda())
+        b.set_populations(torch.from_numpy(df).cuda())
+        a.set_closure(zero)
+        a.step(3)
+        b.step(3)
+        assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
+
+
+def test_closure_fallback_to_rr():
+    """A bound below every prediction sends every cell to the RR update, and
+    each such cell update is counted."""
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(70, 2e-4)
+    p["b3"][:17] = 5.0  # every standardised prediction is large
+    net = B.MLP(C.pack(p))
+    net.set_scaling(mean, inv, out_scale)
+    with B.Solver(B.D3Q27, shape, tau) as a, B.Solver(B.D3Q27, shape, tau) as b:
+        a.set_populations(torch.from_numpy(df).cuda())
+        b.set_populations(torch.from_numpy(df).cuda())
+        a.set_closure(net, bound=1.0)
+        a.step(2)
+        b.step(2)
+        assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
+        assert a.closure_fallbacks() == 2 * int(np.prod(shape))
