@@ -25,6 +25,7 @@ struct lb_ctx {
   double *dout = nullptr;      // reduction result, kRedValues doubles
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
   float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
+  float *ystd = nullptr;       // lazily allocated 17 * n floats: the network's predictions
   const lb_mlp *closure = nullptr;  // learned closure in use (not owned)
   float closure_bound = 0.f;
   unsigned long long *fallbacks = nullptr;  // device counter of cells that fell back to RR
@@ -38,6 +39,7 @@ struct lb_mlp {
   float *gpart = nullptr;      // per-block gradient partials
   float *lpart = nullptr;      // per-block loss partials
   double *dloss = nullptr;
+  int *status = nullptr;       // set to 1 by the tensor-core kernel if a wait timed out
   int nblocks = 0;             // blocks of the training kernel (one per SM)
   long long t = 0;             // Adam steps taken
   int device = 0;
@@ -87,8 +89,10 @@ int free_all(lb_ctx *c) {
   if (c->dout) cudaFree(c->dout);
   if (c->fields) cudaFree(c->fields);
   if (c->mom) cudaFree(c->mom);
+  if (c->ystd) cudaFree(c->ystd);
   if (c->fallbacks) cudaFree(c->fallbacks);
   c->mom = nullptr;
+  c->ystd = nullptr;
   c->fallbacks = nullptr;
   c->f = nullptr;
   c->partials = nullptr;
@@ -244,9 +248,12 @@ int lb_step(lb_ctx *c, int n) {
     if (c->closure) {
       e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
       if (e == cudaSuccess)
-        e = lbrr::launch_step_closure(c->closure->d, static_cast<float *>(c->f), c->g, om1,
-                                      c->parity, c->mom, c->fallbacks, c->closure_bound,
-                                      c->stream);
+        e = lbrr::launch_mlp_tc(c->closure->d, nullptr, c->mom, &c->g, c->g.n, c->ystd,
+                                c->closure->status, c->closure->nblocks, c->stream);
+      if (e == cudaSuccess)
+        e = lbrr::launch_step_delta(c->closure->d, static_cast<float *>(c->f), c->g, om1,
+                                    c->parity, c->ystd, c->fallbacks, c->closure_bound,
+                                    c->stream);
     } else {
       e = lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity,
                             c->stream);
@@ -406,8 +413,9 @@ void lb_mlp_destroy(lb_mlp *m) {
   if (!m) return;
   DeviceGuard dg(m->device);
   if (m->stream) cudaStreamSynchronize(m->stream);
-  void *bufs[] = {m->d.params, m->d.adam_m, m->d.adam_v, m->d.w1,  m->d.w2,  m->d.w3,
-                  m->d.w2t,    m->d.w3t,    m->scaling,  m->gpart, m->lpart, m->dloss};
+  void *bufs[] = {m->d.params, m->d.adam_m, m->d.adam_v, m->d.w1,    m->d.w2,
+                  m->d.w3,     m->d.w2t,    m->d.w3t,    m->scaling, m->gpart,
+                  m->lpart,    m->dloss,    m->status};
   for (void *b : bufs)
     if (b) cudaFree(b);
   delete m;
@@ -439,6 +447,8 @@ int lb_mlp_create(lb_mlp **out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->gpart, 4 * P * (size_t)m->nblocks);
   if (e == cudaSuccess) e = cudaMalloc(&m->lpart, 4 * (size_t)m->nblocks);
   if (e == cudaSuccess) e = cudaMalloc(&m->dloss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     lb_mlp_destroy(m);
@@ -488,6 +498,16 @@ int lb_mlp_set_params(lb_mlp *m, const float *params) {
   return LB_OK;
 }
 
+// LB_ECUDA if a tensor-core wait of the network ever timed out (synchronises).
+static int mlp_status(lb_mlp *m, cudaStream_t st) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "status: %s", cudaGetErrorString(e));
+  if (h) return mlp_fail(m, LB_ECUDA, "a tensor-core wait of the network timed out");
+  return LB_OK;
+}
+
 int lb_mlp_get_params(lb_mlp *m, float *params) {
   if (!m || !params) return mlp_fail(m, LB_EINVAL, "null argument");
   DeviceGuard dg(m->device);
@@ -495,7 +515,7 @@ int lb_mlp_get_params(lb_mlp *m, float *params) {
                                   cudaMemcpyDefault, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "get_params: %s", cudaGetErrorString(e));
-  return LB_OK;
+  return mlp_status(m, m->stream);
 }
 
 int lb_mlp_set_scaling(lb_mlp *m, const float *in_mean, const float *in_inv_std,
@@ -520,9 +540,11 @@ int lb_mlp_forward(lb_mlp *m, const void *X, long long M, float *Y) {
   DeviceGuard dg(m->device);
   const long long tiles = (M + 63) / 64;
   const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
-  cudaError_t e = lbrr::launch_mlp(m->d, X, nullptr, M, Y, nullptr, nullptr, nb, m->stream);
+  (void)nb;
+  cudaError_t e =
+      lbrr::launch_mlp_tc(m->d, X, nullptr, nullptr, M, Y, m->status, m->nblocks, m->stream);
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "forward: %s", cudaGetErrorString(e));
-  return LB_OK;
+  return mlp_status(m, m->stream);
 }
 
 static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
@@ -566,12 +588,13 @@ int lb_mlp_train_step(lb_mlp *m, const void *X, const float *T, long long M, flo
 }
 
 static int ensure_mom(lb_ctx *c) {
-  if (c->mom) return LB_OK;
-  cudaError_t e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
+  if (c->mom && c->ystd) return LB_OK;
+  cudaError_t e = cudaSuccess;
+  if (!c->mom) e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
+  if (e == cudaSuccess && !c->ystd) e = cudaMalloc(&c->ystd, sizeof(float) * 17 * (size_t)c->g.n);
   if (e != cudaSuccess) {
-    c->mom = nullptr;
     cudaGetLastError();
-    return fail(c, LB_ENOMEM, "cannot allocate the moment field");
+    return fail(c, LB_ENOMEM, "cannot allocate the closure fields");
   }
   return LB_OK;
 }
@@ -663,6 +686,13 @@ int lb_closure_fallbacks(lb_ctx *c, long long *count) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "fallback counter");
   *count = (long long)h;
+  if (c->closure) {
+    int st = 0;
+    e = cudaMemcpyAsync(&st, c->closure->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "closure status");
+    if (st) return fail(c, LB_ECUDA, "a tensor-core wait of the network timed out");
+  }
   return LB_OK;
 }
 

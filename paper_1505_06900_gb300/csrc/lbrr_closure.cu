@@ -148,108 +148,33 @@ __global__ void __launch_bounds__(kAux)
 }
 
 // ---------------------------------------------------------- closure step --
-constexpr int kCT = 64;        // cells per block (4 warps x 16 rows of the network)
-constexpr int kCThreads = 128;
-constexpr int kXsC = kMlpIn + 8;
+// One thread per cell (blocks along x, AA parity as in lbrr_step.cu): RR
+// coefficients plus (1 - 1/tau) times the network's correction, RR alone for
+// a cell whose standardised prediction exceeds the bound or whose corrected
+// populations are not all positive (counted).
+constexpr int kDT = 128;
 
 template <int PARITY>
-__global__ void __launch_bounds__(kCThreads)
-    rr_step_closure_kernel(MlpDevice p, float *__restrict__ f, const Grid g, const float om1,
-                           const float *__restrict__ mom, unsigned long long *fallbacks,
-                           const float bound) {
-  __shared__ __align__(16) __nv_bfloat16 xs[kCT][kXsC];
-  __shared__ float da[kCT][kMlpOutUsed + 1];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int g8 = lane >> 2, t4 = lane & 3;
-  const int x0 = blockIdx.x * kCT, y = blockIdx.y, z = blockIdx.z;
-  const long long n = g.n;
-
-  // ---- features of the block's cells (two threads per cell)
-  {
-    const int c = tid & (kCT - 1), half = tid >> 6;
-    const int x = x0 + c;
-    uint32_t *row = reinterpret_cast<uint32_t *>(&xs[c][0]);
-    if (x < g.nx) {
-      for (int nb = half ? 14 : 0; nb < (half ? 27 : 14); ++nb) {
-        const long long cc = nb_cell(g, x, y, z, nb);
-#pragma unroll
-        for (int k = 0; k < kMlpMoments; k += 2) {
-          const float v0 = (__ldg(mom + k * n + cc) - p.in_mean[k]) * p.in_inv_std[k];
-          const float v1 =
-              (__ldg(mom + (k + 1) * n + cc) - p.in_mean[k + 1]) * p.in_inv_std[k + 1];
-          row[(kMlpMoments * nb + k) / 2] = pack_bf16(v0, v1);
-        }
-      }
-      if (half)
-        for (int k = kMlpInUsed; k < kMlpIn; k += 2) row[k / 2] = 0u;
-    } else {
-      for (int k = half * (kMlpIn / 2); k < (half + 1) * (kMlpIn / 2); k += 2) row[k / 2] = 0u;
-    }
-  }
-  __syncthreads();
-
-  // ---- network on the 64 feature rows: warp w owns rows 16w..16w+15
-  {
-    const int r0 = 16 * warp;
-    float h1[8][4] = {};
-#pragma unroll 2
-    for (int ks = 0; ks < kMlpIn / 16; ++ks) {
-      uint32_t a[4];
-      ldsm_x4(a, &xs[r0 + (lane & 15)][16 * ks + 8 * (lane >> 4)]);
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        uint32_t b0, b1;
-        b_frag(b0, b1, p.w1, kMlpIn, 8 * nt, 16 * ks, g8, t4);
-        mma16816(h1[nt], a, b0, b1);
-      }
-    }
-    uint32_t a1[4][4];
-    act_to_frags<8>(h1, p.b1, t4, a1);
-    float h2[8][4] = {};
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        uint32_t b0, b1;
-        b_frag(b0, b1, p.w2, kMlpHidden, 8 * nt, 16 * ks, g8, t4);
-        mma16816(h2[nt], a1[ks], b0, b1);
-      }
-    uint32_t a2[4][4];
-    act_to_frags<8>(h2, p.b2, t4, a2);
-    float yv[3][4] = {};  // outputs 0..23 (17 used)
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-      for (int nt = 0; nt < 3; ++nt) {
-        uint32_t b0, b1;
-        b_frag(b0, b1, p.w3, kMlpHidden, 8 * nt, 16 * ks, g8, t4);
-        mma16816(yv[nt], a2[ks], b0, b1);
-      }
-#pragma unroll
-    for (int nt = 0; nt < 3; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int col = 8 * nt + 2 * t4 + (e & 1), row = r0 + g8 + (e >> 1) * 8;
-        if (col < kMlpOutUsed) da[row][col] = yv[nt][e] + p.b3[col];
-      }
-  }
-  __syncthreads();
-
-  // ---- corrected collision of the block's cells
-  if (tid >= kCT) return;
-  const int x = x0 + tid;
+__global__ void __launch_bounds__(kDT)
+    rr_step_delta_kernel(MlpDevice p, float *__restrict__ f, const Grid g, const float om1,
+                         const float *__restrict__ ystd, unsigned long long *fallbacks,
+                         const float bound) {
+  const int x = blockIdx.x * kDT + threadIdx.x;
   if (x >= g.nx) return;
-  float df[27];
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long n = g.n;
   const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
   const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
   const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
   auto cell_at = [&](int b, int c, int a) -> long long {
     return ((long long)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
   };
+  const long long cell = cell_at(1, 1, 1);
+  float df[27];
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     if (PARITY == 0)
-      df[i] = f[i * n + cell_at(1, 1, 1)];
+      df[i] = f[i * n + cell];
     else
       df[i] = f[(26 - i) * n + cell_at(1 - vel(i, 1), 1 - vel(i, 2), 1 - vel(i, 0))];
   }
@@ -257,25 +182,21 @@ __global__ void __launch_bounds__(kCThreads)
   float c[3][3][3];
   coeffs_rr_d3q27(m, om1, c);
   bool use = true;
-  float dl[kMlpOutUsed];
+  float cc[3][3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) cc[a][b][q] = c[a][b][q];
 #pragma unroll
   for (int k = 0; k < kMlpOutUsed; ++k) {
-    const float yk = da[tid][k];
+    const float yk = __ldg(ystd + k * n + cell);
     use = use && (fabsf(yk) <= bound);  // also false for NaN
-    dl[k] = yk * p.out_scale[k];
+    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yk * p.out_scale[k]);
   }
   float out[27];
   if (use) {
-    float cc[3][3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) cc[a][b][q] = c[a][b][q];
-#pragma unroll
-    for (int k = 0; k < kMlpOutUsed; ++k)
-      cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * dl[k];
     synth_tensor_d3q27<false>(cc, out);
 #pragma unroll
     for (int i = 0; i < 27; ++i) use = use && (out[i] + weight<3>(i) > 0.0f);
@@ -287,7 +208,7 @@ __global__ void __launch_bounds__(kCThreads)
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     if (PARITY == 0)
-      f[(26 - i) * n + cell_at(1, 1, 1)] = out[i];
+      f[(26 - i) * n + cell] = out[i];
     else
       f[i * n + cell_at(1 + vel(i, 1), 1 + vel(i, 2), 1 + vel(i, 0))] = out[i];
   }
@@ -329,14 +250,14 @@ cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int pa
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_closure(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
-                                const float *mom, unsigned long long *fallbacks, float bound,
-                                cudaStream_t st) {
-  const dim3 grid((g.nx + kCT - 1) / kCT, g.ny, g.nz);
+cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
+                              const float *ystd, unsigned long long *fallbacks, float bound,
+                              cudaStream_t st) {
+  const dim3 grid((g.nx + kDT - 1) / kDT, g.ny, g.nz);
   if (parity == 0)
-    rr_step_closure_kernel<0><<<grid, kCThreads, 0, st>>>(p, f, g, om1, mom, fallbacks, bound);
+    rr_step_delta_kernel<0><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound);
   else
-    rr_step_closure_kernel<1><<<grid, kCThreads, 0, st>>>(p, f, g, om1, mom, fallbacks, bound);
+    rr_step_delta_kernel<1><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound);
   return cudaGetLastError();
 }
 

@@ -65,10 +65,16 @@ cudaError_t launch_targets(const MlpDevice &p, int storage, const void *f, const
 // 2x2x2 box average of a fine store into a coarse store (natural order).
 cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int parity_f,
                            int storage_c, void *fc, const Grid &gc, cudaStream_t st);
-// One update of an FP32 D3Q27 store with the learned correction; mom is the
-// moment field of the current populations.
-cudaError_t launch_step_closure(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
-                                const float *mom, unsigned long long *fallbacks, float bound,
-                                cudaStream_t st);
+// Network forward on the tcgen05 tensor cores (lbrr_mlp_tc.cu). With mom:
+// rows are the cells of grid *g, features from the moment field, outputs the
+// 17 standardised predictions Y [17][N]. Without: rows X [M][288] BF16, Y
+// [M][32]. *status becomes 1 if a tensor-core wait timed out.
+cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, const Grid *g,
+                          long long M, float *Y, int *status, int nblocks, cudaStream_t st);
+// One update of an FP32 D3Q27 store with the learned correction: ystd [17][N]
+// holds the network's standardised predictions for the current populations.
+cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
+                              const float *ystd, unsigned long long *fallbacks, float bound,
+                              cudaStream_t st);
 
 }  // namespace lbrr

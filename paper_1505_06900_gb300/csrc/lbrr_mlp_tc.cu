@@ -1,0 +1,358 @@
+// Forward pass of the closure network on the 5th-generation tensor cores
+// (tcgen05, sm_100-family): y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 for
+// tiles of 128 rows, BF16 operands in shared memory, FP32 accumulators in
+// tensor memory (TMEM).
+//
+// One block per SM (persistent). The BF16 weights are staged once into shared
+// memory in the canonical K-major layout without swizzle: 8 x 8 "core
+// matrices" of 128 contiguous bytes (8 rows of 16 bytes), adjacent core
+// matrices along K 128 bytes apart (leading byte offset) and adjacent 8-row
+// groups K/8 * 128 bytes apart (stride byte offset). Per tile the 128 threads
+// write the 128 input rows (thread r owns row r = TMEM lane r) in the same
+// layout; one thread issues the K/16 MMAs of a layer (M = 128, N = 64, 64, 32)
+// and commits them to an mbarrier; the threads then read their row of the
+// accumulator (tcgen05.ld 32x32b), add the bias, apply tanh, round to BF16 and
+// write the next layer's input rows. TMEM columns: layer 1 at 0, layer 2 at 64,
+// layer 3 at 128 (256 allocated).
+//
+// Every mbarrier wait is bounded: on expiry the block records a timeout in
+// *status, waits (bounded) for its MMAs to drain, frees its TMEM and returns.
+#include <cstdint>
+
+#include "lbrr_launch.h"
+#include "lbrr_mlp.h"
+
+namespace lbrr {
+
+namespace {
+
+constexpr int kTcRows = 128;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 256;
+
+// shared-memory plan (bytes, all 1024-aligned)
+constexpr uint32_t kW1Bytes = kMlpHidden * kMlpIn * 2;        // 36864
+constexpr uint32_t kW2Bytes = kMlpHidden * kMlpHidden * 2;    // 8192
+constexpr uint32_t kW3Bytes = kMlpOut * kMlpHidden * 2;       // 4096
+constexpr uint32_t kA1Bytes = kTcRows * kMlpIn * 2;           // 73728
+constexpr uint32_t kA2Bytes = kTcRows * kMlpHidden * 2;       // 16384
+constexpr uint32_t kOffSW1 = 0;
+constexpr uint32_t kOffSW2 = kOffSW1 + kW1Bytes;
+constexpr uint32_t kOffSW3 = kOffSW2 + kW2Bytes;
+constexpr uint32_t kOffSA1 = kOffSW3 + kW3Bytes;
+constexpr uint32_t kOffSA2 = kOffSA1 + kA1Bytes;
+constexpr uint32_t kOffSA3 = kOffSA2 + kA2Bytes;
+constexpr uint32_t kOffMisc = kOffSA3 + kA2Bytes;  // mbarrier, TMEM address, biases
+constexpr uint32_t kTcSmem = kOffMisc + 1024;
+
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+// byte offset of element (row r, column k) of a K-major operand with K columns
+__host__ __device__ constexpr uint32_t cm_offset(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset (K
+// direction), stride byte offset (8-row groups), descriptor version 1, no
+// swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (uint32_t i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(mbar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// make generic-proxy shared-memory writes visible to the tensor core
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// 16 consecutive 32-bit accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// Layer epilogue: tanh(acc + bias) of 64 columns into row r of a K = 64 operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bias,
+                                                unsigned char *dst, int r) {
+#pragma unroll
+  for (int c0 = 0; c0 < kMlpHidden; c0 += 16) {
+    float v[16];
+    tmem_ld16(taddr + c0, v);
+#pragma unroll
+    for (int k = 0; k < 16; k += 8) {
+      uint4 q;
+      q.x = pack2(tanhf(v[k] + bias[c0 + k]), tanhf(v[k + 1] + bias[c0 + k + 1]));
+      q.y = pack2(tanhf(v[k + 2] + bias[c0 + k + 2]), tanhf(v[k + 3] + bias[c0 + k + 3]));
+      q.z = pack2(tanhf(v[k + 4] + bias[c0 + k + 4]), tanhf(v[k + 5] + bias[c0 + k + 5]));
+      q.w = pack2(tanhf(v[k + 6] + bias[c0 + k + 6]), tanhf(v[k + 7] + bias[c0 + k + 7]));
+      *reinterpret_cast<uint4 *>(dst + cm_offset(r, c0 + k, kMlpHidden)) = q;
+    }
+  }
+}
+
+// FROM_MOM: rows are the cells of a grid and their features are built from
+// the moment field mom [10][N]; outputs y[k][cell] for the 17 used outputs.
+// Otherwise rows are X [M][288] (BF16) and outputs Y [M][32].
+template <bool FROM_MOM>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    mlp_tc_kernel(MlpDevice p, const __nv_bfloat16 *__restrict__ X,
+                  const float *__restrict__ mom, const Grid g, long long M,
+                  float *__restrict__ Y, int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int r = threadIdx.x, warp = r >> 5;
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kOffMisc);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc + 8);
+  float *sb = reinterpret_cast<float *>(smem + kOffMisc + 64);  // b1, b2, b3 (160)
+  const uint32_t mbar_a = smem_u32(mbar);
+
+  // ---- weights into the canonical layout; biases
+  for (int c = r; c < kMlpHidden * (kMlpIn / 8); c += kTcThreads) {
+    const int n = c / (kMlpIn / 8), kb = c - n * (kMlpIn / 8);
+    *reinterpret_cast<uint4 *>(smem + kOffSW1 + cm_offset(n, 8 * kb, kMlpIn)) =
+        *reinterpret_cast<const uint4 *>(p.w1 + n * kMlpIn + 8 * kb);
+  }
+  for (int c = r; c < kMlpHidden * (kMlpHidden / 8); c += kTcThreads) {
+    const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
+    *reinterpret_cast<uint4 *>(smem + kOffSW2 + cm_offset(n, 8 * kb, kMlpHidden)) =
+        *reinterpret_cast<const uint4 *>(p.w2 + n * kMlpHidden + 8 * kb);
+  }
+  for (int c = r; c < kMlpOut * (kMlpHidden / 8); c += kTcThreads) {
+    const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
+    *reinterpret_cast<uint4 *>(smem + kOffSW3 + cm_offset(n, 8 * kb, kMlpHidden)) =
+        *reinterpret_cast<const uint4 *>(p.w3 + n * kMlpHidden + 8 * kb);
+  }
+  for (int c = r; c < 2 * kMlpHidden + kMlpOut; c += kTcThreads)
+    sb[c] = c < kMlpHidden ? p.b1[c] : (c < 2 * kMlpHidden ? p.b2[c - kMlpHidden]
+                                                           : p.b3[c - 2 * kMlpHidden]);
+  if (r == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's TMEM lanes
+
+  const uint32_t sw1 = smem_u32(smem + kOffSW1), sw2 = smem_u32(smem + kOffSW2);
+  const uint32_t sw3 = smem_u32(smem + kOffSW3), sa1 = smem_u32(smem + kOffSA1);
+  const uint32_t sa2 = smem_u32(smem + kOffSA2), sa3 = smem_u32(smem + kOffSA3);
+  uint32_t phase = 0;
+  bool ok = true;
+  const long long ntiles = (M + kTcRows - 1) / kTcRows;
+  const long long n = g.n;
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long row = tile * kTcRows + r;
+    const bool valid = row < M;
+    // ---- input row r
+    unsigned char *a1 = smem + kOffSA1;
+    if (FROM_MOM) {
+      // feature 10 nb + k of neighbour nb, written as BF16 pairs in place
+      if (valid) {
+        int x, y, z;
+        cell_coords(row, g, x, y, z);
+#pragma unroll 1
+        for (int nb = 0; nb < 27; ++nb) {
+          const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+          const long long c = ((long long)wrap_add(z, dz, g.nz) * g.ny + wrap_add(y, dy, g.ny)) *
+                                  g.nx + wrap_add(x, dx, g.nx);
+#pragma unroll
+          for (int k = 0; k < kMlpMoments; k += 2) {
+            const float v0 = (__ldg(mom + k * n + c) - p.in_mean[k]) * p.in_inv_std[k];
+            const float v1 =
+                (__ldg(mom + (k + 1) * n + c) - p.in_mean[k + 1]) * p.in_inv_std[k + 1];
+            *reinterpret_cast<uint32_t *>(a1 + cm_offset(r, kMlpMoments * nb + k, kMlpIn)) =
+                pack2(v0, v1);
+          }
+        }
+        for (int f = kMlpInUsed; f < kMlpIn; f += 2)
+          *reinterpret_cast<uint32_t *>(a1 + cm_offset(r, f, kMlpIn)) = 0u;
+      } else {
+        for (int kb = 0; kb < kMlpIn / 8; ++kb)
+          *reinterpret_cast<uint4 *>(a1 + cm_offset(r, 8 * kb, kMlpIn)) =
+              make_uint4(0u, 0u, 0u, 0u);
+      }
+    } else {
+#pragma unroll 4
+      for (int kb = 0; kb < kMlpIn / 8; ++kb) {
+        const uint4 q = valid ? *reinterpret_cast<const uint4 *>(X + row * kMlpIn + 8 * kb)
+                              : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4 *>(a1 + cm_offset(r, 8 * kb, kMlpIn)) = q;
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // ---- layer 1: D[128 x 64] (TMEM cols 0..63) = A1[128 x 288] W1^T
+    if (r == 0) {
+#pragma unroll 1
+      for (int ks = 0; ks < kMlpIn / 16; ++ks)
+        umma(tmem, sdesc(sa1 + 256 * ks, 128, (kMlpIn / 8) * 128),
+             sdesc(sw1 + 256 * ks, 128, (kMlpIn / 8) * 128), idesc_bf16(128, 64), ks > 0);
+      umma_commit(mbar_a);
+    }
+    ok = !__syncthreads_or(!mbar_wait(mbar_a, phase));  // same decision in every thread
+    phase ^= 1;
+    fence_after();
+    if (!ok) break;
+    hidden_epilogue(lane_addr + 0, sb, smem + kOffSA2, r);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // ---- layer 2 (TMEM cols 64..127)
+    if (r == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kMlpHidden / 16; ++ks)
+        umma(tmem + 64, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+             sdesc(sw2 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(128, 64), ks > 0);
+      umma_commit(mbar_a);
+    }
+    ok = !__syncthreads_or(!mbar_wait(mbar_a, phase));  // same decision in every thread
+    phase ^= 1;
+    fence_after();
+    if (!ok) break;
+    hidden_epilogue(lane_addr + 64, sb + kMlpHidden, smem + kOffSA3, r);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // ---- layer 3 (TMEM cols 128..159)
+    if (r == 0) {
+#pragma unroll
+      for (int ks = 0; ks < kMlpHidden / 16; ++ks)
+        umma(tmem + 128, sdesc(sa3 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+             sdesc(sw3 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(128, 32), ks > 0);
+      umma_commit(mbar_a);
+    }
+    ok = !__syncthreads_or(!mbar_wait(mbar_a, phase));  // same decision in every thread
+    phase ^= 1;
+    fence_after();
+    if (!ok) break;
+    float y[32];
+    tmem_ld16(lane_addr + 128, *reinterpret_cast<float(*)[16]>(&y[0]));
+    tmem_ld16(lane_addr + 144, *reinterpret_cast<float(*)[16]>(&y[16]));
+    if (valid) {
+      const float *b3 = sb + 2 * kMlpHidden;
+      if (FROM_MOM) {
+#pragma unroll
+        for (int k = 0; k < kMlpOutUsed; ++k) Y[k * M + row] = y[k] + b3[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < kMlpOut; k += 4)
+          *reinterpret_cast<float4 *>(Y + row * kMlpOut + k) =
+              make_float4(y[k] + b3[k], y[k + 1] + b3[k + 1], y[k + 2] + b3[k + 2],
+                          y[k + 3] + b3[k + 3]);
+      }
+    }
+    fence_before();
+    __syncthreads();  // the next tile overwrites A1 and the accumulators
+    fence_after();
+  }
+
+  if (!ok) {
+    if (r == 0) atomicExch(status, 1);
+    // let any MMA still in flight finish before the memory goes away
+    mbar_wait(mbar_a, phase);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, const Grid *g,
+                          long long M, float *Y, int *status, int nblocks, cudaStream_t st) {
+  const bool from_mom = mom != nullptr;
+  cudaError_t e = cudaFuncSetAttribute(from_mom ? mlp_tc_kernel<true> : mlp_tc_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = (M + kTcRows - 1) / kTcRows;
+  const int nb = (int)(tiles < nblocks ? tiles : nblocks);
+  const Grid gg = g ? *g : Grid{1, 1, 1, M};
+  if (from_mom)
+    mlp_tc_kernel<true><<<nb, kTcThreads, kTcSmem, st>>>(p, nullptr, mom, gg, M, Y, status);
+  else
+    mlp_tc_kernel<false><<<nb, kTcThreads, kTcSmem, st>>>(
+        p, static_cast<const __nv_bfloat16 *>(X), nullptr, gg, M, Y, status);
+  return cudaGetLastError();
+}
+
+}  // namespace lbrr
