@@ -94,7 +94,10 @@ def generate_dataset(n_fine: int, mach: float, re: float, seeds, snapshots, frac
         picks[(si, ki)] = idx
         targs.append(coarse.closure_targets(raw).index_select(0, idx))
     mean = s1 / cnt
-    std = torch.sqrt(torch.clamp(s2 / cnt - mean * mean, min=1e-60))
+    std = torch.sqrt(torch.clamp(s2 / cnt - mean * mean, min=0.0))
+    # a moment kind that barely varies (e.g. a velocity component that stays
+    # zero) must not turn round-off into large standardised features
+    std = torch.maximum(std, 1e-3 * std.max())
     T = torch.cat(targs)
     out_scale = T[:, :17].double().pow(2).mean(0).sqrt().clamp_min(1e-30)
     T[:, :17] = (T[:, :17].double() / out_scale).float()

@@ -56,16 +56,24 @@ __device__ __forceinline__ void b_frag(uint32_t &b0, uint32_t &b1, const __nv_bf
 }
 
 // A fragments of the next layer from NT accumulator tiles (bias + tanh first).
+// Hardware tanh (tanh.approx.f32, relative error ~2^-11, below the BF16
+// rounding the activations get next); the same in training and inference.
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 template <int NT>
 __device__ __forceinline__ void act_to_frags(float (&acc)[NT][4], const float *bias, int t,
                                              uint32_t (&a)[NT / 2][4]) {
 #pragma unroll
   for (int nt = 0; nt < NT; ++nt) {
     const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
-    acc[nt][0] = tanhf(acc[nt][0] + b0);
-    acc[nt][1] = tanhf(acc[nt][1] + b1);
-    acc[nt][2] = tanhf(acc[nt][2] + b0);
-    acc[nt][3] = tanhf(acc[nt][3] + b1);
+    acc[nt][0] = tanh_approx(acc[nt][0] + b0);
+    acc[nt][1] = tanh_approx(acc[nt][1] + b1);
+    acc[nt][2] = tanh_approx(acc[nt][2] + b0);
+    acc[nt][3] = tanh_approx(acc[nt][3] + b1);
   }
 #pragma unroll
   for (int ks = 0; ks < NT / 2; ++ks) {

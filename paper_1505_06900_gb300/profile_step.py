@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--lattice", type=int, default=27, choices=[9, 27])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--closure", action="store_true",
+                    help="run the learned-closure update (D3Q27, FP32) with small random weights")
     args = ap.parse_args()
     build_mod.build()
     storage = {"f32": B.STORE_F32, "f16": B.STORE_F16, "bf16": B.STORE_BF16}[args.storage]
@@ -40,15 +42,24 @@ def main():
         shape = (n, n, 1)
         rho, u = W.taylor_green_2d(n, 0.05)
         tau = W.taylor_green_2d_tau(n, 0.05)
+    net = None
     with B.Solver(args.lattice, shape, tau, storage=storage) as s:
         s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
                       torch.from_numpy(u.astype(np.float32)).cuda())
+        if args.closure:
+            rng = np.random.default_rng(0)
+            params = (0.02 * rng.standard_normal(B.MLP_PARAMS)).astype(np.float32)
+            net = B.MLP(params)
+            net.set_scaling(np.zeros(10), np.full(10, 10.0), np.full(17, 1e-6))
+            s.set_closure(net, bound=1e6)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s.step(args.steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         d = s.diagnostics()
+    if net is not None:
+        net.close()
     cells = int(np.prod(shape))
     print(f"lattice D{2 if args.lattice == 9 else 3}Q{args.lattice} {shape} {args.storage}: "
           f"{args.steps} steps in {dt * 1e3:.2f} ms ({cells * args.steps / dt / 1e9:.2f} GLUPS), "

@@ -163,8 +163,7 @@ def test_features_targets_and_coarsening_match_oracle():
     assert max_rel_to_weight(O.D3Q27, cg, shifted(O.D3Q27, C.coarsen(f))) <= 1e-6
 
 
-def _closure_case(seed, out_scale_value):
-    shape = (64 + 16, 3, 4)  # two 64-cell tiles, the second ragged
+def _closure_case(seed, out_scale_value, shape=(64 + 16, 3, 4)):
     rng = np.random.default_rng(seed)
     rho, u = W.random_field(shape, 3, seed=seed, a_rho=0.005, a_u=0.03)
     tau = 0.6
@@ -178,10 +177,16 @@ def _closure_case(seed, out_scale_value):
     return shape, tau, df, p, mean.astype(np.float32), inv.astype(np.float32), out_scale
 
 
-def test_closure_step_matches_oracle_and_zero_network_is_rr():
+# nx = 80: the network gathers each row's features from the moment field;
+# nx = 128: it stages the neighbour rows of a 128-cell row segment first.
+# (Every extent is >= 3: with 2 cells along an axis the periodic central
+# difference vanishes, a moment kind has zero variance and its
+# standardisation amplifies round-off.)
+@pytest.mark.parametrize("shape", [(80, 3, 4), (128, 3, 3)])
+def test_closure_step_matches_oracle_and_zero_network_is_rr(shape):
     """Two closure updates against the reference with the network evaluated at
     the kernels' precision (BF16 features and hidden layers)."""
-    shape, tau, df, p, mean, inv, out_scale = _closure_case(60, 2e-5)
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(60, 2e-5, shape)
     net = B.MLP(C.pack(p))
     net.set_scaling(mean, inv, out_scale)
     with B.Solver(B.D3Q27, shape, tau) as s:
