@@ -61,6 +61,8 @@ extern "C" {
 /* collision models */
 #define LB_COLLIDE_RR 0   /* recursive regularized, Sec. 3.4 (the paper's model) */
 #define LB_COLLIDE_REG2 1 /* order-2 regularized comparator, Sec. 3.6.1 (eq_feq_2) */
+#define LB_COLLIDE_BGK 2  /* plain BGK, f - (f - f0)/tau with the full-basis f0 of Sec. 3.2
+                             (eq_full_discr_bgk, Sec. 3.3); initialised like RR */
 
 /* initialisation modes of lb_init_fields */
 #define LB_INIT_EQ 0        /* f = f0(rho, u) */

@@ -28,6 +28,7 @@ D2Q9 = 9
 D3Q27 = 27
 RR = 0        # recursive-regularized model (Sec. 3.4)
 REG2 = 1      # order-2 regularized comparator (Sec. 3.6.1)
+BGK = 2       # plain BGK with the full-basis equilibrium (Sec. 3.3)
 INIT_EQ = 0
 INIT_EQ_NEQ_FD = 1
 

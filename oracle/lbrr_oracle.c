@@ -20,7 +20,8 @@
  *                                  plain two-array pull update.
  *
  * The order-2 regularized model of Sec. 3.6.1 (eq_feq_2) is the comparator
- * variant ORA_REG2. Everything is plain loops in double precision; no
+ * variant ORA_REG2; ORA_BGK is the plain BGK update of Sec. 3.3
+ * (eq_full_discr_bgk) with the same full-basis equilibrium. Everything is plain loops in double precision; no
  * blocking, fusion or reordering beyond the formulas. Population arrays are
  * laid out f[i][z][y][x] (x fastest), i = (cx+1) + 3(cy+1) + 9(cz+1).
  *
@@ -46,6 +47,7 @@
 #define ORA_D3Q27 27
 #define ORA_RR 0
 #define ORA_REG2 1
+#define ORA_BGK 2
 #define ORA_INIT_EQ 0
 #define ORA_INIT_EQ_NEQ_FD 1
 
@@ -161,6 +163,7 @@ static void equilibrium_coefficients(double rho, const double u[3], hcoef *a) {
  * cut at order two (eq_feq_2). */
 static double feq(const ora_lattice *L, int variant, int i, double rho, const double u[3]) {
   hcoef a;
+  if (variant == ORA_BGK) variant = ORA_RR;
   double j[3] = {rho * u[0], rho * u[1], rho * u[2]};
   equilibrium_coefficients(rho, u, &a);
   if (variant == ORA_REG2) {
@@ -215,6 +218,7 @@ static void recursive_coefficients(int d, const double u[3], hcoef *a) {
  * ORA_REG2 only the order-two term is kept (Sec. 3.6.1). */
 static double fneq(const ora_lattice *L, int variant, int i, const hcoef *a1) {
   const double zero[3] = {0.0, 0.0, 0.0};
+  if (variant == ORA_BGK) variant = ORA_RR;
   if (variant == ORA_REG2) {
     hcoef a2;
     memset(&a2, 0, sizeof a2);
@@ -265,6 +269,11 @@ static void collide_cell(const ora_lattice *L, int variant, double tau, const do
   double rho, u[3];
   hcoef a1;
   density_velocity(L, f, &rho, u);
+  if (variant == ORA_BGK) {
+    /* eq_full_discr_bgk: f_post = f - (f - f0) / tau */
+    for (int i = 0; i < L->q; ++i) fpost[i] = f[i] - (f[i] - feq(L, ORA_RR, i, rho, u)) / tau;
+    return;
+  }
   neq_stress(L, variant, f, rho, u, &a1);
   recursive_coefficients(L->d, u, &a1);
   for (int i = 0; i < L->q; ++i)

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "liblbrr.so")
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED = 0, 1, 2, 3, 4
 D2Q9, D3Q27 = 9, 27
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
-COLLIDE_RR, COLLIDE_REG2 = 0, 1
+COLLIDE_RR, COLLIDE_REG2, COLLIDE_BGK = 0, 1, 2
 INIT_EQ, INIT_EQ_NEQ_FD = 0, 1
 
 # every entry point of include/lbrr.h with its ctypes signature

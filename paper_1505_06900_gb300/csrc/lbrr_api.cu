@@ -160,7 +160,8 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   if (opt->periodic != 1) return fail(nullptr, LB_EINVAL, "only fully periodic grids are supported");
   if (opt->storage < LB_STORE_F32 || opt->storage > LB_STORE_BF16)
     return fail(nullptr, LB_EINVAL, "unknown storage %d", opt->storage);
-  if (opt->collision != LB_COLLIDE_RR && opt->collision != LB_COLLIDE_REG2)
+  if (opt->collision != LB_COLLIDE_RR && opt->collision != LB_COLLIDE_REG2 &&
+      opt->collision != LB_COLLIDE_BGK)
     return fail(nullptr, LB_EINVAL, "unknown collision model %d", opt->collision);
   const long long n = (long long)opt->nx * opt->ny * opt->nz;
   if (n > (1LL << 40)) return fail(nullptr, LB_EINVAL, "grid too large");

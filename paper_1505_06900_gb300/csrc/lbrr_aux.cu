@@ -259,7 +259,7 @@ cudaError_t launch_init(int q, int storage, int model, void *f, const Grid &g, c
     constexpr int Q_ = decltype(qc)::value;
     constexpr int S_ = decltype(sc)::value;
     using T = typename Storage<S_>::T;
-    if (model == 0)
+    if (model != 1)  // RR and BGK contexts start from the full-basis f0 + f1
       init_kernel<Q_, S_, 0><<<cells_grid(g.n), kAuxThreads, 0, st>>>(static_cast<T *>(f), g,
                                                                         rho, u, tau, mode);
     else

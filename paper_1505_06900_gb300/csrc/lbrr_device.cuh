@@ -340,7 +340,8 @@ __device__ __forceinline__ void coeffs_reg2_d3q27(const Macro &m, float om1,
 
 // moments<G>(f): macroscopic moments of one cell (G: f holds g = df / w).
 // synth<MODEL, G>(m, om1, f): post-collision populations (MODEL 0: RR,
-// 1: order-2 regularized) as df, or as g with G.
+// 1: order-2 regularized, 2: plain BGK f - (f - f0)/tau, for which f holds the
+// pre-collision populations on entry) as df, or as g with G.
 template <int Q>
 struct Lattice;
 template <>
@@ -353,6 +354,14 @@ struct Lattice<9> {
   template <int MODEL, bool G = false>
   __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[9]) {
     float c[3][3];
+    if (MODEL == 2) {  // equilibrium coefficients only, then relax
+      coeffs_rr_d2q9(m, 0.0f, c);
+      float eq[9];
+      synth_tensor_d2q9<G>(c, eq);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[i] = fmaf(1.0f - om1, eq[i] - f[i], f[i]);
+      return;
+    }
     if (MODEL == 0)
       coeffs_rr_d2q9(m, om1, c);
     else
@@ -370,6 +379,14 @@ struct Lattice<27> {
   template <int MODEL, bool G = false>
   __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[27]) {
     float c[3][3][3];
+    if (MODEL == 2) {  // equilibrium coefficients only, then relax
+      coeffs_rr_d3q27(m, 0.0f, c);
+      float eq[27];
+      synth_tensor_d3q27<G>(c, eq);
+#pragma unroll
+      for (int i = 0; i < 27; ++i) f[i] = fmaf(1.0f - om1, eq[i] - f[i], f[i]);
+      return;
+    }
     if (MODEL == 0)
       coeffs_rr_d3q27(m, om1, c);
     else

@@ -89,8 +89,11 @@ static cudaError_t step_t(void *f, const Grid &g, float om1, int parity, cudaStr
 template <int Q, int S>
 static cudaError_t step_m(int model, void *f, const Grid &g, float om1, int parity,
                           cudaStream_t st) {
-  return model == 0 ? step_t<Q, S, 0>(f, g, om1, parity, st)
-                    : step_t<Q, S, 1>(f, g, om1, parity, st);
+  switch (model) {
+    case 0: return step_t<Q, S, 0>(f, g, om1, parity, st);
+    case 1: return step_t<Q, S, 1>(f, g, om1, parity, st);
+    default: return step_t<Q, S, 2>(f, g, om1, parity, st);
+  }
 }
 
 template <int Q>

@@ -159,20 +159,23 @@ static cudaError_t tiled_t(void *f, const Grid &g, float om1, int parity, cudaSt
 
 bool tiled16_supported(const Grid &g) { return g.nx % kTileX == 0; }
 
+template <int Q, int S>
+static cudaError_t tiled_m(int model, void *f, const Grid &g, float om1, int parity,
+                           cudaStream_t st) {
+  switch (model) {
+    case 0: return tiled_t<Q, S, 0>(f, g, om1, parity, st);
+    case 1: return tiled_t<Q, S, 1>(f, g, om1, parity, st);
+    default: return tiled_t<Q, S, 2>(f, g, om1, parity, st);
+  }
+}
+
 cudaError_t launch_step_tiled16(int q, int storage, int model, void *f, const Grid &g, float om1,
                                 int parity, cudaStream_t st) {
-  if (q == 9) {
-    if (storage == 1)
-      return model == 0 ? tiled_t<9, 1, 0>(f, g, om1, parity, st)
-                        : tiled_t<9, 1, 1>(f, g, om1, parity, st);
-    return model == 0 ? tiled_t<9, 2, 0>(f, g, om1, parity, st)
-                      : tiled_t<9, 2, 1>(f, g, om1, parity, st);
-  }
-  if (storage == 1)
-    return model == 0 ? tiled_t<27, 1, 0>(f, g, om1, parity, st)
-                      : tiled_t<27, 1, 1>(f, g, om1, parity, st);
-  return model == 0 ? tiled_t<27, 2, 0>(f, g, om1, parity, st)
-                    : tiled_t<27, 2, 1>(f, g, om1, parity, st);
+  if (q == 9)
+    return storage == 1 ? tiled_m<9, 1>(model, f, g, om1, parity, st)
+                        : tiled_m<9, 2>(model, f, g, om1, parity, st);
+  return storage == 1 ? tiled_m<27, 1>(model, f, g, om1, parity, st)
+                      : tiled_m<27, 2>(model, f, g, om1, parity, st);
 }
 
 }  // namespace lbrr

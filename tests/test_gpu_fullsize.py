@@ -85,3 +85,100 @@ def test_sampled_cells_at_512_cubed():
     # conservation at full size
     assert abs(d2[0] - d0[0]) <= 1e-12 * d0[0]
     assert np.allclose(d2[1:4], d0[1:4], rtol=0, atol=1e-3)
+
+
+def _sample_two_steps(lattice, N3, df_dev, samples, tau, storage=None):
+    """Run two updates from df_dev ([Q, nz, ny, nx] shifted populations on the
+    device) and return the logical populations of the sampled cells after each."""
+    from paper_1505_06900_gb300 import binding as B
+    nx, ny, nz = N3
+    q = df_dev.shape[0]
+    got = []
+    kw = {} if storage is None else {"storage": storage}
+    with B.Solver(lattice, N3, tau, **kw) as s:
+        s.set_populations(df_dev)
+        for _ in range(2):
+            s.step(1)
+            out = s.populations()
+            idx = torch.tensor([(z * ny + y) * nx + x for (x, y, z) in samples], device="cuda")
+            got.append(out.view(q, -1).index_select(1, idx).cpu().numpy().astype(np.float64))
+            del out
+            torch.cuda.empty_cache()
+    return got
+
+
+def test_sampled_cells_d2q9_2048_squared():
+    """D2Q9 2048^2 (the double-shear-layer size), FP32 store: sampled cells
+    after one and two updates against the oracle's collisions."""
+    from paper_1505_06900_gb300 import binding as B
+    n = 2048
+    c, w = O.lattice_tables(O.D2Q9)
+    tau = W.double_shear_2d_tau(n, 0.1)
+    gen = torch.Generator(device="cuda").manual_seed(77)
+    wt = torch.tensor(w, dtype=torch.float32, device="cuda").view(9, 1, 1, 1)
+    df = torch.randn((9, 1, n, n), generator=gen, device="cuda", dtype=torch.float32) * (0.05 * wt)
+    rng = np.random.default_rng(7)
+    samples = [(0, 0, 0), (n - 1, n - 1, 0), (0, n - 1, 0), (n - 1, 0, 0)]
+    samples += [(int(rng.integers(0, n)), int(rng.integers(0, n)), 0) for _ in range(30)]
+    host = {}
+    for (x, y, _) in samples:
+        ix = torch.tensor([(x + d) % n for d in range(-2, 3)], device="cuda")
+        iy = torch.tensor([(y + d) % n for d in range(-2, 3)], device="cuda")
+        host[(x, y)] = (df[:, 0].index_select(2, ix).index_select(1, iy).cpu().numpy()
+                        .astype(np.float64) + w.reshape(9, 1, 1))
+    got = _sample_two_steps(B.D2Q9, (n, n, 1), df, samples, tau)
+    for si, (x, y, _) in enumerate(samples):
+        h = host[(x, y)]
+        cache = {}
+
+        def post(dx, dy):
+            if (dx, dy) not in cache:
+                cache[(dx, dy)] = O.collide_cell(O.D2Q9, h[:, 2 + dy, 2 + dx], tau)
+            return cache[(dx, dy)]
+
+        ref1 = np.array([post(-c[i, 0], -c[i, 1])[i] for i in range(9)]) - w
+        assert np.max(np.abs(got[0][:, si] - ref1) / w) <= 1e-6
+        ref2 = np.array([O.collide_cell(O.D2Q9, np.array(
+            [post(-c[i, 0] - c[j, 0], -c[i, 1] - c[j, 1])[j] for j in range(9)]), tau)[i]
+            for i in range(9)]) - w
+        assert np.max(np.abs(got[1][:, si] - ref2) / w) <= 1e-6
+
+
+def test_sampled_cells_f16_store_at_512_cubed():
+    """D3Q27 512^3 with the FP16 store (the shared-memory tiled kernel the
+    benchmark's FP16 variant times): one update of sampled cells, stored value
+    within one FP16 unit in the last place (plus 1e-6) of the oracle's."""
+    from paper_1505_06900_gb300 import binding as B
+    c, w = O.lattice_tables(O.D3Q27)
+    free = torch.cuda.mem_get_info()[0]
+    if free < 40e9:
+        pytest.skip("needs 40 GB of free device memory")
+    gen = torch.Generator(device="cuda").manual_seed(99)
+    g16 = (0.05 * torch.randn((27, N, N, N), generator=gen, device="cuda")).to(torch.float16)
+    rng = np.random.default_rng(9)
+    samples = [(0, 0, 0), (N - 1, N - 1, N - 1), (127, 128, 5), (128, 0, N - 1)]
+    samples += [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(12)]
+    hoods = {}
+    for (x, y, z) in samples:
+        ix = torch.tensor([(x + d) % N for d in (-1, 0, 1)], device="cuda")
+        iy = torch.tensor([(y + d) % N for d in (-1, 0, 1)], device="cuda")
+        iz = torch.tensor([(z + d) % N for d in (-1, 0, 1)], device="cuda")
+        sub = g16.index_select(3, ix).index_select(2, iy).index_select(1, iz)
+        hoods[(x, y, z)] = w.reshape(27, 1, 1, 1) * (1.0 + sub.cpu().numpy().astype(np.float64))
+    with B.Solver(B.D3Q27, (N, N, N), TAU, storage=B.STORE_F16) as s:
+        s.set_state(g16.contiguous().view(torch.uint8).reshape(-1), 0)
+        del g16
+        torch.cuda.empty_cache()
+        s.step(1)
+        out = s.populations()
+        idx = torch.tensor([(z * N + y) * N + x for (x, y, z) in samples], device="cuda")
+        got = out.view(27, -1).index_select(1, idx).cpu().numpy().astype(np.float64)
+        del out
+    for si, smp in enumerate(samples):
+        h = hoods[smp]
+        ref = np.array([O.collide_cell(O.D3Q27, h[:, 1 - c[i, 2], 1 - c[i, 1], 1 - c[i, 0]], TAU)[i]
+                        for i in range(27)])
+        g_ref = ref / w - 1.0
+        g_got = got[:, si] / w
+        ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(g_ref), 2.0 ** -14))) - 10)
+        assert np.all(np.abs(g_got - g_ref) <= ulp + 1e-6), smp

@@ -59,20 +59,22 @@ def raw_store(g: np.ndarray, storage: int, parity: int, c: np.ndarray) -> "torch
 
 @pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16])
 @pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("collision", [B.COLLIDE_RR, B.COLLIDE_BGK])
 # nx a multiple of 128 takes the shared-memory tiled kernel, other nx the
 # one-thread-per-cell kernel
 @pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (260, 5, 1)), (O.D2Q9, (256, 3, 1)),
                                            (O.D3Q27, (140, 5, 4)), (O.D3Q27, (256, 3, 4))])
-def test_one_update_is_correctly_rounded(storage, parity, lattice, shape):
+def test_one_update_is_correctly_rounded(storage, parity, collision, lattice, shape):
     """Both AA kernels (the store is written at either parity from the host)."""
+    variant = O.RR if collision == B.COLLIDE_RR else O.BGK
     _, q = O.dims_of(lattice)
     c, _ = O.lattice_tables(lattice)
     w = weights(lattice).reshape(-1, 1, 1, 1)
     df = W.random_populations(q, shape, seed=31 + parity, amp=0.05)
     g_in = round16(df / w, storage)            # what the 16-bit store holds
-    f_ref = O.step(lattice, shape, 0.63, w * (1.0 + g_in), 1)
+    f_ref = O.step(lattice, shape, 0.63, w * (1.0 + g_in), 1, variant)
     g_ref = f_ref / w - 1.0
-    with B.Solver(lattice, shape, 0.63, storage=storage) as s:
+    with B.Solver(lattice, shape, 0.63, storage=storage, collision=collision) as s:
         raw = raw_store(g_in, storage, parity, c)
         assert raw.numel() == s.state_bytes()
         s.set_state(raw, parity)

@@ -44,12 +44,12 @@ def _solver(lattice, shape, tau, storage=B.STORE_F32, collision=B.COLLIDE_RR):
 
 
 @pytest.mark.parametrize("lattice,shape", CASES)
-@pytest.mark.parametrize("collision", [B.COLLIDE_RR, B.COLLIDE_REG2])
+@pytest.mark.parametrize("collision", [B.COLLIDE_RR, B.COLLIDE_REG2, B.COLLIDE_BGK])
 def test_steps_match_oracle(lattice, shape, collision):
     """Updates 1, 2 and 3 (both AA kernels) against the oracle's pull update."""
     tau = 0.62
     df = _random_state(lattice, shape, seed=100 + lattice)
-    variant = O.RR if collision == B.COLLIDE_RR else O.REG2
+    variant = {B.COLLIDE_RR: O.RR, B.COLLIDE_REG2: O.REG2, B.COLLIDE_BGK: O.BGK}[collision]
     with _solver(lattice, shape, tau, collision=collision) as s:
         s.set_populations(_cuda(df))
         f = f64_state(lattice, df)

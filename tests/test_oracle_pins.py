@@ -242,7 +242,7 @@ def test_fneq_at_rest_is_order_two(lat):
 # -------------------------------------------------------------- collision ----
 
 @pytest.mark.parametrize("lat", LATTICES)
-@pytest.mark.parametrize("variant", [O.RR, O.REG2])
+@pytest.mark.parametrize("variant", [O.RR, O.REG2, O.BGK])
 def test_collision_moments(lat, variant):
     """eq_discr_bgk_reg: post-collision populations keep rho and rho u and
     relax the non-equilibrium stress, sum xi xi f_post = rho cs2 I + rho u u +
@@ -267,6 +267,25 @@ def test_collision_moments(lat, variant):
         assert abs(r2 - rho) < 1e-15 and np.allclose(u2, u, atol=1e-15)
         iu = np.triu_indices(d)
         assert np.allclose(p2, Pi[iu], atol=1e-15)
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+def test_bgk_relaxes_every_hermite_coefficient(lat):
+    """eq_full_discr_bgk: plain BGK scales every Hermite coefficient of
+    f - f0 by (1 - 1/tau), the ones of order > 2 included (which RR replaces by
+    the recursion)."""
+    _, w = O.lattice_tables(lat)
+    d, q = O.dims_of(lat)
+    H, _ = O.hermite_basis(lat)
+    rng = np.random.default_rng(12)
+    f = w * (1 + 0.1 * rng.standard_normal(q))
+    rho, u, _ = O.moments_cell(lat, f)
+    f0 = O.feq_cell(lat, rho, u)
+    for tau in (0.6, 1.7):
+        post = O.collide_cell(lat, f, tau, O.BGK)
+        assert np.allclose(H @ (post - f0), (1 - 1 / tau) * (H @ (f - f0)), atol=1e-15)
+        rr = O.collide_cell(lat, f, tau, O.RR)
+        assert np.abs(H[1 + d + d * (d + 1) // 2:] @ (rr - post)).max() > 1e-6
 
 
 @pytest.mark.parametrize("lat", LATTICES)
