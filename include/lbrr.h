@@ -108,7 +108,9 @@ LB_API int lb_set_stream(lb_ctx *ctx, void *stream);
 LB_API int lb_init_fields(lb_ctx *ctx, const float *rho, const float *u, int init_mode);
 
 /* Advance n >= 0 full collide-and-stream updates (eq_discr_bgk_reg). n == 0 is
- * a no-op. Asynchronous on the context's stream. */
+ * a no-op. Asynchronous on the context's stream. With a 16-bit store the
+ * update waits (boundedly) for its own bulk copies; if such a wait ever
+ * expires, the next lb_diagnostics or lb_get_state returns LB_ECUDA. */
 LB_API int lb_step(lb_ctx *ctx, int n);
 
 /* Macroscopic fields of the current populations into device buffers:

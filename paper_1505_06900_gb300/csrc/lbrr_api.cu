@@ -23,6 +23,7 @@ struct lb_ctx {
   void *f = nullptr;       // population store, q * n elements
   double *partials = nullptr;  // reduction scratch, kRedBlocks * kRedValues doubles
   double *dout = nullptr;      // reduction result, kRedValues doubles
+  int *status = nullptr;       // set to 1 by the 16-bit row kernel if a bounded wait expired
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
   float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
   float *ystd = nullptr;       // lazily allocated 17 * n floats: the network's predictions
@@ -87,6 +88,8 @@ int free_all(lb_ctx *c) {
   if (c->f) cudaFree(c->f);
   if (c->partials) cudaFree(c->partials);
   if (c->dout) cudaFree(c->dout);
+  if (c->status) cudaFree(c->status);
+  c->status = nullptr;
   if (c->fields) cudaFree(c->fields);
   if (c->mom) cudaFree(c->mom);
   if (c->ystd) cudaFree(c->ystd);
@@ -119,9 +122,13 @@ int diagnostics(lb_ctx *c, double *out) {
                                            c->dout, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics launch");
   double h[lbrr::kRedValues];
+  int st = 0;
   e = cudaMemcpyAsync(h, c->dout, sizeof h, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics copy");
+  if (st) return fail(c, LB_ECUDA, "a bulk-copy wait of the 16-bit step kernel timed out");
   out[0] = (double)c->g.n + h[0];
   for (int a = 0; a < c->d; ++a) out[1 + a] = h[1 + a];
   out[1 + c->d] = h[4];
@@ -186,6 +193,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   if (e == cudaSuccess)
     e = cudaMalloc(&c->partials, sizeof(double) * lbrr::kRedBlocks * lbrr::kRedValues);
   if (e == cudaSuccess) e = cudaMalloc(&c->dout, sizeof(double) * lbrr::kRedValues);
+  if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);
@@ -194,6 +202,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   }
   // rest state: df = 0 in every storage precision
   e = cudaMemset(c->f, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_all(c);
@@ -257,7 +266,7 @@ int lb_step(lb_ctx *c, int n) {
                                     c->stream);
     } else {
       e = lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity,
-                            c->stream);
+                            c->status, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->parity ^= 1;
@@ -330,10 +339,14 @@ int lb_get_state(lb_ctx *c, void *dst, int *parity) {
   LB_CHECK_CTX(c);
   if (!dst || !parity) return fail(c, LB_EINVAL, "null argument");
   DeviceGuard dg(c->device);
+  int st = 0;
   cudaError_t e = cudaMemcpyAsync(dst, c->f, (size_t)lb_state_bytes(c), cudaMemcpyDefault,
                                   c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
+  if (st) return fail(c, LB_ECUDA, "a bulk-copy wait of the 16-bit step kernel timed out");
   *parity = c->parity;
   return LB_OK;
 }

@@ -15,9 +15,17 @@ constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3,
 // One collide-and-stream update of the AA store `f` (element type given by
 // `storage`): parity 0 reads and writes the cell's own slots (writing the
 // post-collision population i into slot opp(i)); parity 1 reads slot opp(i)
-// of x - xi_i and writes slot i of x + xi_i.
+// of x - xi_i and writes slot i of x + xi_i. *status becomes 1 if a bounded
+// wait of the 16-bit row kernel expired (the update is then incomplete).
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
-                        int parity, cudaStream_t st);
+                        int parity, int *status, cudaStream_t st);
+
+// The persistent row kernel for 16-bit stores (lbrr_step16.cu): sets
+// launched = false, launching nothing, where it does not apply (nx not a
+// multiple of 16, nx < 64, nx above 1024 (D3Q27) or 2048 (D2Q9), or no
+// block fits on an SM).
+cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid &g, float om1,
+                              int parity, int *status, cudaStream_t st, bool &launched);
 
 // The shared-memory tiled variant of launch_step for 16-bit stores
 // (lbrr_step16.cu); usable when tiled16_supported(g) (nx a multiple of 128).

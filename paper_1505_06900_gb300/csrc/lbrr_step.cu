@@ -107,9 +107,15 @@ static cudaError_t step_s(int storage, int model, void *f, const Grid &g, float 
 }
 
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
-                        int parity, cudaStream_t st) {
-  if (storage != 0 && tiled16_supported(g))
-    return launch_step_tiled16(q, storage, model, f, g, om1, parity, st);
+                        int parity, int *status, cudaStream_t st) {
+  // 16-bit stores: row segments of 128 cells where nx allows (the fastest),
+  // else whole rows, else one thread per cell
+  if (storage != 0) {
+    if (tiled16_supported(g)) return launch_step_tiled16(q, storage, model, f, g, om1, parity, st);
+    bool launched = false;
+    cudaError_t e = launch_step_row16(q, storage, model, f, g, om1, parity, status, st, launched);
+    if (e != cudaSuccess || launched) return e;
+  }
   return q == 9 ? step_s<9>(storage, model, f, g, om1, parity, st)
                 : step_s<27>(storage, model, f, g, om1, parity, st);
 }
