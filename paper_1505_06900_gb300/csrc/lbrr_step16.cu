@@ -3,7 +3,8 @@
 //
 // With 2-byte populations a one-thread-per-cell kernel issues one memory
 // instruction per 2 bytes and keeps too few bytes in flight to saturate HBM.
-// Here a block owns one row segment of kTileX cells at (y, z). It stages, for
+// Here a block owns one row segment of TX cells at (y, z) (TX = 256 where nx
+// allows, else 128; TX / 2 threads). It stages, for
 // each of the Q slots, the 16-byte chunks of the row that slot is read from
 // (cp.async, 16 bytes per copy), including an 8-value halo on both sides for
 // the x +- 1 shifts of the odd AA update; each thread then collides two
@@ -19,7 +20,7 @@
 // x - xi_i and writes slot i of x + xi_i. Slot s is therefore read from and
 // written to the same row (y + cy_s, z + cz_s) in an odd update. A location
 // outside the block's cells may be read as halo while its owner rewrites it;
-// the value is never used. Requires nx to be a multiple of kTileX.
+// the value is never used. Requires nx to be a multiple of TX.
 #include <algorithm>
 
 #include "lbrr_launch.h"
@@ -27,10 +28,8 @@
 
 namespace lbrr {
 
-constexpr int kTileX = 128;                    // cells per block, two per thread
-constexpr int kThreads16 = kTileX / 2;
+constexpr int kTileX = 128;                    // shortest row segment (cells per block)
 constexpr int kHalo = 8;                       // one 16-byte chunk of halo per side
-constexpr int kRowLen = kTileX + 2 * kHalo;    // staged values per slot
 constexpr int kChunk = 8;                      // 16-bit values per 16-byte chunk
 
 template <int S>
@@ -67,17 +66,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
-template <int Q, int S, int MODEL, int PARITY>
-__global__ void __launch_bounds__(kThreads16)
+template <int Q, int S, int MODEL, int PARITY, int TX>
+__global__ void __launch_bounds__(TX / 2)
     rr_step_tiled16_kernel(typename Storage<S>::T *__restrict__ f, const Grid g, const float om1) {
   using T = typename Storage<S>::T;
   using T2 = typename Half<S>::T2;
   constexpr int D = Lattice<Q>::D;
-  constexpr int kInner = kTileX / kChunk;  // chunks of the block's own cells per slot
-  __shared__ __align__(16) T tile[Q][kRowLen];
+  constexpr int kThreads = TX / 2;         // two cells per thread
+  constexpr int kInner = TX / kChunk;      // chunks of the block's own cells per slot
+  __shared__ __align__(16) T tile[Q][TX + 2 * kHalo];
 
   const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * kTileX;
+  const int x0 = blockIdx.x * TX;
   const int y = blockIdx.y, z = blockIdx.z;
   const long long n = g.n;
 
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kThreads16)
 
   // Chunk loops: thread tid moves chunk k = tid % kInner of the slots
   // s = tid / kInner + j * kSlotStep, j = 0, 1, ...
-  constexpr int kSlotStep = kThreads16 / kInner;
+  constexpr int kSlotStep = kThreads / kInner;
   constexpr int kSlotIters = (Q + kSlotStep - 1) / kSlotStep;
   const int kc = tid % kInner, s0 = tid / kInner;
 
@@ -109,12 +109,12 @@ __global__ void __launch_bounds__(kThreads16)
   }
   // ... and, for the odd update, one halo chunk on each side (periodic in x)
   if (PARITY) {
-    static_assert(2 * Q <= kThreads16, "one halo chunk per thread");
+    static_assert(2 * Q <= kThreads, "one halo chunk per thread");
     if (tid < 2 * Q) {
       const int s = tid >> 1, side = tid & 1;
-      const int xg = side ? (x0 + kTileX == g.nx ? 0 : x0 + kTileX)
+      const int xg = side ? (x0 + TX == g.nx ? 0 : x0 + TX)
                           : (x0 == 0 ? g.nx - kChunk : x0 - kChunk);
-      cp_async16(&tile[s][side ? kHalo + kTileX : 0], slot_row(s) + xg);
+      cp_async16(&tile[s][side ? kHalo + TX : 0], slot_row(s) + xg);
     }
   }
   cp_async_wait_all();
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kThreads16)
   __syncthreads();
 
   // ---- store the values this block owns. Slot s of an odd update owns the
-  // tile positions [kHalo + cx_s, kHalo + kTileX + cx_s): whole 16-byte chunks
+  // tile positions [kHalo + cx_s, kHalo + TX + cx_s): whole 16-byte chunks
   // go out as vector stores, the 8 values per shifted slot that share a chunk
   // with a neighbouring segment one by one.
   // Slots with cx = +1 are s % 3 == 2, with cx = -1 s % 3 == 0 (bit masks).
@@ -170,14 +170,14 @@ __global__ void __launch_bounds__(kThreads16)
     // m = p / 8 (s = 3 (m / 2) for cx = -1, 3 (m / 2) + 2 for cx = +1), value t
     constexpr int kEdgeItems = 2 * Q / 3 * kChunk;
 #pragma unroll
-    for (int p = tid; p < kEdgeItems; p += kThreads16) {
+    for (int p = tid; p < kEdgeItems; p += kThreads) {
       const int m = p / kChunk, t = p % kChunk;
       const bool pos = m & 1;
       const int s = 3 * (m >> 1) + (pos ? 2 : 0);
-      // cx = +1: positions kHalo+1 .. kHalo+7 and kHalo+kTileX
-      // cx = -1: positions kHalo-1 and kHalo+kTileX-8 .. kHalo+kTileX-2
-      const int j = pos ? (t < kChunk - 1 ? kHalo + 1 + t : kHalo + kTileX)
-                        : (t == 0 ? kHalo - 1 : kHalo + kTileX - kChunk - 1 + t);
+      // cx = +1: positions kHalo+1 .. kHalo+7 and kHalo+TX
+      // cx = -1: positions kHalo-1 and kHalo+TX-8 .. kHalo+TX-2
+      const int j = pos ? (t < kChunk - 1 ? kHalo + 1 + t : kHalo + TX)
+                        : (t == 0 ? kHalo - 1 : kHalo + TX - kChunk - 1 + t);
       int xg = x0 - kHalo + j;
       xg = xg < 0 ? xg + g.nx : (xg >= g.nx ? xg - g.nx : xg);
       slot_row(s)[xg] = tile[s][j];
@@ -445,15 +445,21 @@ cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid
                       : row_m<27, 2>(model, f, g, om1, parity, status, st, launched);
 }
 
+template <int Q, int S, int MODEL, int TX>
+static cudaError_t tiled_tx(void *f, const Grid &g, float om1, int parity, cudaStream_t st) {
+  using T = typename Storage<S>::T;
+  const dim3 grid(g.nx / TX, g.ny, g.nz);
+  if (parity == 0)
+    rr_step_tiled16_kernel<Q, S, MODEL, 0, TX><<<grid, TX / 2, 0, st>>>(static_cast<T *>(f), g, om1);
+  else
+    rr_step_tiled16_kernel<Q, S, MODEL, 1, TX><<<grid, TX / 2, 0, st>>>(static_cast<T *>(f), g, om1);
+  return cudaGetLastError();
+}
+
 template <int Q, int S, int MODEL>
 static cudaError_t tiled_t(void *f, const Grid &g, float om1, int parity, cudaStream_t st) {
-  using T = typename Storage<S>::T;
-  const dim3 grid(g.nx / kTileX, g.ny, g.nz);
-  if (parity == 0)
-    rr_step_tiled16_kernel<Q, S, MODEL, 0><<<grid, kThreads16, 0, st>>>(static_cast<T *>(f), g, om1);
-  else
-    rr_step_tiled16_kernel<Q, S, MODEL, 1><<<grid, kThreads16, 0, st>>>(static_cast<T *>(f), g, om1);
-  return cudaGetLastError();
+  if (g.nx % 256 == 0) return tiled_tx<Q, S, MODEL, 256>(f, g, om1, parity, st);
+  return tiled_tx<Q, S, MODEL, 128>(f, g, om1, parity, st);
 }
 
 bool tiled16_supported(const Grid &g) { return g.nx % kTileX == 0; }
