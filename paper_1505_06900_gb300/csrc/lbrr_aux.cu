@@ -155,26 +155,69 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double *out) {
   }
 }
 
-template <int Q, int S>
+// Mass, momentum and kinetic energy of the logical populations. Work items
+// are chunks of kRedThreads cells of one row (y, z), a block taking items
+// blockIdx.x, blockIdx.x + gridDim.x, ... and each thread one cell of the
+// item. Logical population i of cell x is slot i at x (parity 0) or slot
+// s = opp(i) at x + cx_s of row (y + cy_s, z + cz_s) (parity 1); the Q
+// slot-row offsets are computed once per item. Per-cell values are formed in
+// FP32 and summed over up to kDiagFlush cells in FP32, then accumulated in
+// FP64 (FP64 arithmetic is slow on this GPU); the order is fixed, so results
+// are reproducible run to run.
+constexpr int kDiagFlush = 8;
+
+template <int Q, int S, int PARITY>
 __global__ void __launch_bounds__(kRedThreads)
     diag_partial_kernel(const typename Storage<S>::T *__restrict__ f, const Grid g,
-                        const int parity, double *__restrict__ partials) {
+                        double *__restrict__ partials) {
+  constexpr int D = Lattice<Q>::D;
+  __shared__ long long srow[Q];
   double acc[kRedValues] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  const long long stride = (long long)gridDim.x * kRedThreads;
-  for (long long cell = (long long)blockIdx.x * kRedThreads + threadIdx.x; cell < g.n;
-       cell += stride) {
-    int x, y, z;
-    cell_coords(cell, g, x, y, z);
-    float df[Q];
-    load_logical<Q, S>(f, g, parity, x, y, z, df);
-    const Macro m = Lattice<Q>::moments(df);
-    const double jx = m.jx, jy = m.jy, jz = m.jz;
-    acc[0] += (double)m.drho;
-    acc[1] += jx;
-    acc[2] += jy;
-    acc[3] += jz;
-    acc[4] += 0.5 * (jx * jx + jy * jy + jz * jz) / (double)m.rho;
+  float part[kRedValues] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  int pending = 0;
+  const int chunks = (g.nx + kRedThreads - 1) / kRedThreads;
+  const long long items = (long long)g.ny * g.nz * chunks;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int r = (int)(it / chunks), x = (int)(it - (long long)r * chunks) * kRedThreads + threadIdx.x;
+    __syncthreads();  // the previous item's offsets are no longer read
+    if (threadIdx.x < Q) {
+      const int sl = threadIdx.x;
+      int y = r % g.ny, z = r / g.ny;
+      if (PARITY) {
+        y = wrap_add(y, vel(sl, 1), g.ny);
+        z = D == 3 ? wrap_add(z, vel(sl, 2), g.nz) : 0;
+      }
+      srow[sl] = (long long)sl * g.n + ((long long)z * g.ny + y) * g.nx;
+    }
+    __syncthreads();
+    if (x < g.nx) {
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xp = x + 1 == g.nx ? 0 : x + 1;
+      float df[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int sl = PARITY ? Q - 1 - i : i;
+        const int cx = PARITY ? vel(sl, 0) : 0;
+        const int xs = cx < 0 ? xm : (cx > 0 ? xp : x);
+        df[i] = Storage<S>::template load<D>(f + srow[sl] + xs, i);
+      }
+      const Macro m = Lattice<Q>::moments(df);
+      part[0] += m.drho;
+      part[1] += m.jx;
+      part[2] += m.jy;
+      part[3] += m.jz;
+      part[4] += 0.5f * (m.jx * m.ux + m.jy * m.uy + m.jz * m.uz);
+      if (++pending == kDiagFlush) {
+#pragma unroll
+        for (int k = 0; k < kRedValues; ++k) {
+          acc[k] += (double)part[k];
+          part[k] = 0.f;
+        }
+        pending = 0;
+      }
+    }
   }
+#pragma unroll
+  for (int k = 0; k < kRedValues; ++k) acc[k] += (double)part[k];
   block_sum<kRedValues>(acc, partials + (long long)blockIdx.x * kRedValues);
 }
 
@@ -312,8 +355,12 @@ cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g,
     constexpr int Q_ = decltype(qc)::value;
     constexpr int S_ = decltype(sc)::value;
     using T = typename Storage<S_>::T;
-    diag_partial_kernel<Q_, S_><<<nb, kRedThreads, 0, st>>>(static_cast<const T *>(f), g, parity,
-                                                            partials);
+    if (parity)
+      diag_partial_kernel<Q_, S_, 1><<<nb, kRedThreads, 0, st>>>(static_cast<const T *>(f), g,
+                                                                 partials);
+    else
+      diag_partial_kernel<Q_, S_, 0><<<nb, kRedThreads, 0, st>>>(static_cast<const T *>(f), g,
+                                                                 partials);
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -328,8 +375,12 @@ cudaError_t launch_diagnostics_blocks(int q, int storage, const void *f, const G
     constexpr int Q_ = decltype(qc)::value;
     constexpr int S_ = decltype(sc)::value;
     using T = typename Storage<S_>::T;
-    diag_partial_kernel<Q_, S_><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T *>(f), g,
-                                                                 parity, partials);
+    if (parity)
+      diag_partial_kernel<Q_, S_, 1><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T *>(f),
+                                                                      g, partials);
+    else
+      diag_partial_kernel<Q_, S_, 0><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T *>(f),
+                                                                      g, partials);
   });
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
