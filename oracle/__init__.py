@@ -72,6 +72,10 @@ def _load():
                 "ora_diagnostics": [i, i, i, i, dp, dp],
                 "ora_enstrophy": [i, i, i, i, dp, dp],
                 "ora_collide_cell_closure": [d, dp, dp, dp],
+                "ora_step_walls": [i, i, i, i, i, d, i, dp, i],
+                "ora_init_walls": [i, i, i, i, i, d, i, i, dp, dp, dp],
+                "ora_fields_walls": [i, i, i, i, i, i, dp, dp, dp, dp],
+                "ora_enstrophy_walls": [i, i, i, i, i, dp, dp],
                 "ora_num_threads": [],
                 "ora_set_num_threads": [i],
             }
@@ -194,8 +198,10 @@ def collide_cell_closure(f, tau: float, delta) -> np.ndarray:
 
 
 def init(lattice: int, shape, tau: float, rho, u, mode: int = INIT_EQ_NEQ_FD,
-         variant: int = RR) -> np.ndarray:
-    """Initial populations f [Q, nz, ny, nx] from rho [nz,ny,nx], u [D,nz,ny,nx]."""
+         variant: int = RR, walls: int = 0) -> np.ndarray:
+    """Initial populations f [Q, nz, ny, nx] from rho [nz,ny,nx], u [D,nz,ny,nx].
+    walls: bit a = no-slip walls through the end node planes of axis a (the
+    boundary nodes start at rest)."""
     lib = _load()
     D, Q = dims_of(lattice)
     nx, ny, nz = shape
@@ -203,23 +209,35 @@ def init(lattice: int, shape, tau: float, rho, u, mode: int = INIT_EQ_NEQ_FD,
     uu = _f64(u).reshape(-1)
     assert r.size == nx * ny * nz and uu.size == D * r.size
     f = np.zeros(Q * r.size)
-    _check(lib.ora_init(lattice, variant, nx, ny, nz, float(tau), mode, _dp(r), _dp(uu), _dp(f)),
-           "init")
+    if walls:
+        _check(lib.ora_init_walls(lattice, variant, nx, ny, nz, float(tau), mode, int(walls),
+                                  _dp(r), _dp(uu), _dp(f)), "init_walls")
+    else:
+        _check(lib.ora_init(lattice, variant, nx, ny, nz, float(tau), mode, _dp(r), _dp(uu),
+                            _dp(f)), "init")
     return f.reshape(Q, nz, ny, nx)
 
 
 def step(lattice: int, shape, tau: float, f: np.ndarray, nsteps: int = 1,
-         variant: int = RR) -> np.ndarray:
-    """Return the populations after nsteps updates (the input is not modified)."""
+         variant: int = RR, walls: int = 0) -> np.ndarray:
+    """Return the populations after nsteps updates (the input is not modified).
+    With walls, populations that stream in from outside the domain are NaN
+    in the result (the boundary rule rebuilds them)."""
     lib = _load()
     nx, ny, nz = shape
     out = np.array(f, dtype=np.float64, order="C", copy=True)
-    _check(lib.ora_step(lattice, variant, nx, ny, nz, float(tau), _dp(out), int(nsteps)), "step")
+    if walls:
+        _check(lib.ora_step_walls(lattice, variant, nx, ny, nz, float(tau), int(walls), _dp(out),
+                                  int(nsteps)), "step_walls")
+    else:
+        _check(lib.ora_step(lattice, variant, nx, ny, nz, float(tau), _dp(out), int(nsteps)),
+               "step")
     return out
 
 
-def fields(lattice: int, shape, f: np.ndarray, variant: int = RR):
-    """(rho [nz,ny,nx], u [D,...], pi1 [3|6,...]) of a population field."""
+def fields(lattice: int, shape, f: np.ndarray, variant: int = RR, walls: int = 0):
+    """(rho [nz,ny,nx], u [D,...], pi1 [3|6,...]) of a population field; with
+    walls, boundary nodes report their regularized state (u = 0)."""
     lib = _load()
     D, _ = dims_of(lattice)
     nx, ny, nz = shape
@@ -228,26 +246,42 @@ def fields(lattice: int, shape, f: np.ndarray, variant: int = RR):
     rho = np.zeros(n)
     u = np.zeros(D * n)
     p = np.zeros((3 if D == 2 else 6) * n)
-    _check(lib.ora_fields(lattice, variant, nx, ny, nz, _dp(ff), _dp(rho), _dp(u), _dp(p)),
-           "fields")
+    if walls:
+        _check(lib.ora_fields_walls(lattice, variant, nx, ny, nz, int(walls), _dp(ff), _dp(rho),
+                                    _dp(u), _dp(p)), "fields_walls")
+    else:
+        _check(lib.ora_fields(lattice, variant, nx, ny, nz, _dp(ff), _dp(rho), _dp(u), _dp(p)),
+               "fields")
     return rho.reshape(nz, ny, nx), u.reshape(D, nz, ny, nx), p.reshape(-1, nz, ny, nx)
 
 
-def diagnostics(lattice: int, shape, f: np.ndarray) -> np.ndarray:
-    """[mass, momentum_0..D-1, kinetic energy]."""
+def diagnostics(lattice: int, shape, f: np.ndarray, walls: int = 0) -> np.ndarray:
+    """[mass, momentum_0..D-1, kinetic energy]; with walls, of the fields of
+    fields(..., walls) (plain sums over the nodes)."""
     lib = _load()
     D, _ = dims_of(lattice)
     nx, ny, nz = shape
+    if walls:
+        rho, u, _ = fields(lattice, shape, f, walls=walls)
+        mom = [float(np.sum(rho * u[a])) for a in range(D)]
+        return np.array([float(np.sum(rho))] + mom + [float(0.5 * np.sum(rho * np.sum(u * u, 0)))])
     out = np.zeros(2 + D)
     _check(lib.ora_diagnostics(lattice, nx, ny, nz, _dp(_f64(f)), _dp(out)), "diagnostics")
     return out
 
 
-def enstrophy(lattice: int, shape, f: np.ndarray) -> float:
+def enstrophy(lattice: int, shape, f: np.ndarray, walls: int = 0) -> float:
+    """0.5 sum |curl u|^2 over the cells (periodic central differences); with
+    walls, the trapezoidal rule over the nodes with one-sided differences on
+    the wall planes."""
     lib = _load()
     nx, ny, nz = shape
     out = np.zeros(1)
-    _check(lib.ora_enstrophy(lattice, nx, ny, nz, _dp(_f64(f)), _dp(out)), "enstrophy")
+    if walls:
+        _check(lib.ora_enstrophy_walls(lattice, nx, ny, nz, int(walls), _dp(_f64(f)), _dp(out)),
+               "enstrophy_walls")
+    else:
+        _check(lib.ora_enstrophy(lattice, nx, ny, nz, _dp(_f64(f)), _dp(out)), "enstrophy")
     return float(out[0])
 
 

@@ -19,6 +19,12 @@
  *   streaming f_i(x + xi_i, t+1)  (eq_discr_bgk_reg), periodic wrap, with a
  *                                  plain two-array pull update.
  *
+ * No-slip walls (Sec. 3.5, boundary conditions): the regularized Dirichlet
+ * procedure with u_bc = 0 on boundary nodes that lie on the walls (rho from
+ * the lattice symmetries, f0(rho, u_bc), Pi^(1) from the symmetries,
+ * f1 = w / (2 cs^4) H2 : Pi^(1), all populations replaced by f0 + f1), then
+ * the usual collision; see wall_regularize.
+ *
  * The order-2 regularized model of Sec. 3.6.1 (eq_feq_2) is the comparator
  * variant ORA_REG2; ORA_BGK is the plain BGK update of Sec. 3.3
  * (eq_full_discr_bgk) with the same full-basis equilibrium. Everything is plain loops in double precision; no
@@ -32,6 +38,11 @@
  *  - Hermite polynomials: the paper defers to Grad; the standard tensor
  *    Hermite polynomials with variance c_s^2 are used (H_xxy = (x^2-cs2) y ...).
  *  - Appendix B, 2D a1^(4)_xxyy: the printed "a^(3)_xxy" is read as a1^(3)_xxy.
+ *  - Walls: populations of a buried link (a population and its opposite both
+ *    streaming in from outside, on edges and corners) are taken at
+ *    equilibrium when rho is formed; boundary nodes start at rest; the
+ *    enstrophy with walls is the trapezoidal rule over the nodes with
+ *    second-order one-sided differences on the wall planes.
  *  - The initial non-equilibrium stress uses a1^(2) = -2 c_s^2 rho tau S
  *    (Sec. 3.3 CE result) with tau the scheme's tau-bar, S by periodic second
  *    order central differences.
@@ -617,6 +628,266 @@ int ora_enstrophy(int lattice, int nx, int ny, int nz, const double *f, double *
     s += 0.5 * (wx * wx + wy * wy + wz * wz);
   }
   free(u);
+  *out = s;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* No-slip walls (Sec. 3.5, the boundary-conditions paragraph)               */
+/*                                                                          */
+/* walls: bit a set = axis a is bounded by no-slip walls that pass through   */
+/* its first and last node planes (the boundary nodes lie on the walls and   */
+/* carry u_bc = 0); the other axes stay periodic. A population of a node is  */
+/* unknown when the node it streams from, x - xi_i, lies outside the domain.  */
+
+/* 1 if node p has unknown populations; unknown[i] marks them. */
+static int unknown_set(const ora_lattice *L, int walls, const long p[3], const long dims[3],
+                       int *unknown) {
+  int any = 0;
+  for (int i = 0; i < L->q; ++i) {
+    unknown[i] = 0;
+    for (int a = 0; a < L->d; ++a) {
+      if (!((walls >> a) & 1)) continue;
+      const long s = p[a] - L->c[i][a];
+      if (s < 0 || s >= dims[a]) unknown[i] = 1;
+    }
+    any |= unknown[i];
+  }
+  return any;
+}
+
+/* The regularized Dirichlet procedure with u_bc = 0, step by step as the
+ * paper describes it (after Latt et al. 2008):
+ *  1. rho from the lattice symmetries: with zero wall velocity the unknown
+ *     populations carry as much mass as their known opposites, so
+ *     rho = sum of the known populations whose opposite is known
+ *         + 2 x sum of the known populations whose opposite is unknown.
+ *     Reading for buried links (a population and its opposite both unknown,
+ *     on edges and corners): they are taken at equilibrium, w_i rho, so the
+ *     sum above equals rho (1 - sum of their weights).
+ *  2. f0_i(rho, u_bc) (eq_fzero with u = 0).
+ *  3. Pi^(1) from the symmetries: the off-equilibrium part of an unknown
+ *     population is that of its opposite (zero for buried links), and
+ *     Pi^(1) = sum_i H2_i f1_i.
+ *  4. f1_i = w_i / (2 cs^4) H2_i : Pi^(1), which is eq_fone at u = 0 (the
+ *     recursion's higher orders vanish there).
+ *  5. every population of the node is replaced by f0_i + f1_i (eq_reg).
+ * freg receives the regularized populations. */
+static void wall_regularize(const ora_lattice *L, int variant, const double *f,
+                            const int *unknown, double *freg) {
+  const double zero[3] = {0.0, 0.0, 0.0};
+  double s = 0.0, wb = 0.0;
+  for (int i = 0; i < L->q; ++i) {
+    const int o = L->q - 1 - i;
+    if (!unknown[i])
+      s += unknown[o] ? 2.0 * f[i] : f[i];
+    else if (unknown[o])
+      wb += L->w[i];
+  }
+  const double rho = s / (1.0 - wb);
+  double f1[27];
+  for (int i = 0; i < L->q; ++i) {
+    const int o = L->q - 1 - i;
+    if (!unknown[i])
+      f1[i] = f[i] - feq(L, variant, i, rho, zero);
+    else if (!unknown[o])
+      f1[i] = f[o] - feq(L, variant, o, rho, zero);
+    else
+      f1[i] = 0.0;
+  }
+  double S[3][3] = {{0}};
+  for (int i = 0; i < L->q; ++i)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        S[a][b] += (L->c[i][a] * L->c[i][b] - (a == b ? cs2 : 0.0)) * f1[i];
+  hcoef a1;
+  memset(&a1, 0, sizeof a1);
+  a1.xx = S[0][0];
+  a1.xy = S[0][1];
+  a1.yy = S[1][1];
+  if (L->d == 3) {
+    a1.xz = S[0][2];
+    a1.yz = S[1][2];
+    a1.zz = S[2][2];
+  }
+  recursive_coefficients(L->d, zero, &a1);
+  for (int i = 0; i < L->q; ++i) freg[i] = feq(L, variant, i, rho, zero) + fneq(L, variant, i, &a1);
+}
+
+static int check_walls(const ora_lattice *L, int walls, int nx, int ny, int nz) {
+  const int dims[3] = {nx, ny, nz};
+  if (walls < 0 || walls >= (1 << L->d)) return -1;
+  for (int a = 0; a < L->d; ++a)
+    if (((walls >> a) & 1) && dims[a] < 3) return -1;
+  return 0;
+}
+
+/* nsteps updates of eq_discr_bgk_reg with no-slip walls on the axes in
+ * `walls`: every boundary node is regularized (wall_regularize) and then
+ * collided like any other node; the pull streaming leaves the populations
+ * that would come from outside the domain undefined (NaN), to be rebuilt by
+ * the next regularization. */
+int ora_step_walls(int lattice, int variant, int nx, int ny, int nz, double tau, int walls,
+                   double *f, int nsteps) {
+  ora_lattice L;
+  if (make_lattice(lattice, &L)) return -1;
+  if (nx <= 0 || ny <= 0 || nz <= 0 || (L.d == 2 && nz != 1) || nsteps < 0) return -1;
+  if (check_walls(&L, walls, nx, ny, nz)) return -1;
+  const long n = (long)nx * ny * nz;
+  const long dims[3] = {nx, ny, nz};
+  double *post = (double *)malloc(sizeof(double) * L.q * n);
+  if (!post) return -2;
+  for (int s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+    for (long cell = 0; cell < n; ++cell) {
+      const long p[3] = {cell % nx, (cell / nx) % ny, cell / ((long)nx * ny)};
+      double fc[27], fr[27], fp[27];
+      int unknown[27];
+      for (int i = 0; i < L.q; ++i) fc[i] = f[i * n + cell];
+      if (unknown_set(&L, walls, p, dims, unknown)) {
+        wall_regularize(&L, variant, fc, unknown, fr);
+        collide_cell(&L, variant, tau, fr, fp);
+      } else {
+        collide_cell(&L, variant, tau, fc, fp);
+      }
+      for (int i = 0; i < L.q; ++i) post[i * n + cell] = fp[i];
+    }
+#pragma omp parallel for schedule(static)
+    for (long cell = 0; cell < n; ++cell) {
+      const long p[3] = {cell % nx, (cell / nx) % ny, cell / ((long)nx * ny)};
+      for (int i = 0; i < L.q; ++i) {
+        long q[3];
+        int out = 0;
+        for (int a = 0; a < 3; ++a) {
+          q[a] = p[a] - L.c[i][a];
+          if ((walls >> a) & 1)
+            out |= q[a] < 0 || q[a] >= dims[a];
+          else
+            q[a] = wrap(q[a], dims[a]);
+        }
+        f[i * n + cell] = out ? NAN : post[i * n + (q[2] * ny + q[1]) * nx + q[0]];
+      }
+    }
+  }
+  free(post);
+  return 0;
+}
+
+/* Initial populations with walls: as ora_init for the nodes off the walls
+ * (their central differences never cross a wall); the boundary nodes start
+ * at rest, f = f0(rho, 0). */
+int ora_init_walls(int lattice, int variant, int nx, int ny, int nz, double tau, int mode,
+                   int walls, const double *rho, const double *u, double *f) {
+  ora_lattice L;
+  if (make_lattice(lattice, &L)) return -1;
+  if (check_walls(&L, walls, nx, ny, nz)) return -1;
+  int rc = ora_init(lattice, variant, nx, ny, nz, tau, mode, rho, u, f);
+  if (rc) return rc;
+  const long n = (long)nx * ny * nz;
+  const long dims[3] = {nx, ny, nz};
+  const double zero[3] = {0.0, 0.0, 0.0};
+  for (long cell = 0; cell < n; ++cell) {
+    const long p[3] = {cell % nx, (cell / nx) % ny, cell / ((long)nx * ny)};
+    int unknown[27];
+    if (unknown_set(&L, walls, p, dims, unknown))
+      for (int i = 0; i < L.q; ++i) f[i * n + cell] = feq(&L, variant, i, rho[cell], zero);
+  }
+  return 0;
+}
+
+/* Macroscopic fields with walls: a boundary node reports those of its
+ * regularized populations (rho of the symmetry rule, u = u_bc = 0, Pi^(1)). */
+int ora_fields_walls(int lattice, int variant, int nx, int ny, int nz, int walls, const double *f,
+                     double *rho, double *u, double *pi1) {
+  ora_lattice L;
+  if (make_lattice(lattice, &L)) return -1;
+  if (check_walls(&L, walls, nx, ny, nz)) return -1;
+  const long n = (long)nx * ny * nz;
+  const long dims[3] = {nx, ny, nz};
+  const int np = L.d == 2 ? 3 : 6;
+#pragma omp parallel for schedule(static)
+  for (long cell = 0; cell < n; ++cell) {
+    const long p[3] = {cell % nx, (cell / nx) % ny, cell / ((long)nx * ny)};
+    double fc[27], fr[27], r, uu[3], pp[6];
+    int unknown[27];
+    for (int i = 0; i < L.q; ++i) fc[i] = f[i * n + cell];
+    if (unknown_set(&L, walls, p, dims, unknown)) {
+      wall_regularize(&L, variant, fc, unknown, fr);
+      memcpy(fc, fr, sizeof fr);
+    }
+    ora_moments_cell(lattice, variant, fc, &r, uu, pp);
+    rho[cell] = r;
+    for (int a = 0; a < L.d; ++a) u[a * n + cell] = uu[a];
+    for (int k = 0; k < np; ++k) pi1[k * n + cell] = pp[k];
+  }
+  return 0;
+}
+
+/* d u_comp / d x_axis at node p with walls: second-order one-sided
+ * differences on the wall planes of a walled axis, central differences
+ * elsewhere (periodic across the faces of periodic axes). */
+static double wall_at(const double *uc, int axis, const long p[3], const long dims[3], long k) {
+  long q[3] = {p[0], p[1], p[2]};
+  q[axis] = k;
+  return uc[(q[2] * dims[1] + q[1]) * dims[0] + q[0]];
+}
+
+static double wall_diff(const double *u, int comp, int axis, const long p[3], const long dims[3],
+                        int walls) {
+  const long n = dims[0] * dims[1] * dims[2];
+  const double *uc = u + comp * n;
+  const long m = dims[axis], a = p[axis];
+  if ((walls >> axis) & 1) {
+    if (a == 0)
+      return 0.5 * (-3.0 * wall_at(uc, axis, p, dims, 0) + 4.0 * wall_at(uc, axis, p, dims, 1) -
+                    wall_at(uc, axis, p, dims, 2));
+    if (a == m - 1)
+      return 0.5 * (3.0 * wall_at(uc, axis, p, dims, m - 1) -
+                    4.0 * wall_at(uc, axis, p, dims, m - 2) + wall_at(uc, axis, p, dims, m - 3));
+    return 0.5 * (wall_at(uc, axis, p, dims, a + 1) - wall_at(uc, axis, p, dims, a - 1));
+  }
+  return 0.5 * (wall_at(uc, axis, p, dims, wrap(a + 1, m)) -
+                wall_at(uc, axis, p, dims, wrap(a - 1, m)));
+}
+
+/* Enstrophy with walls, the trapezoidal rule of 0.5 |curl u|^2 over the
+ * nodes (weight 1/2 on each wall plane a node lies on), velocities of
+ * ora_fields_walls, derivatives of wall_diff. In lattice units: the
+ * dimensionless 0.5 int omega^2 dA of Sec. 4.1 is this sum / U_lb^2. */
+int ora_enstrophy_walls(int lattice, int nx, int ny, int nz, int walls, const double *f,
+                        double *out) {
+  ora_lattice L;
+  if (make_lattice(lattice, &L)) return -1;
+  if (check_walls(&L, walls, nx, ny, nz)) return -1;
+  const long n = (long)nx * ny * nz;
+  const long dims[3] = {nx, ny, nz};
+  double *rho = (double *)malloc(sizeof(double) * n);
+  double *u = (double *)calloc(3 * n, sizeof(double));
+  double *pi = (double *)malloc(sizeof(double) * 6 * n);
+  if (!rho || !u || !pi) {
+    free(rho);
+    free(u);
+    free(pi);
+    return -2;
+  }
+  ora_fields_walls(lattice, ORA_RR, nx, ny, nz, walls, f, rho, u, pi);
+  double s = 0.0;
+  for (long cell = 0; cell < n; ++cell) {
+    const long p[3] = {cell % nx, (cell / nx) % ny, cell / ((long)nx * ny)};
+    double wgt = 1.0;
+    for (int a = 0; a < L.d; ++a)
+      if (((walls >> a) & 1) && (p[a] == 0 || p[a] == dims[a] - 1)) wgt *= 0.5;
+    double wx = 0.0, wy = 0.0;
+    const double wz = wall_diff(u, 1, 0, p, dims, walls) - wall_diff(u, 0, 1, p, dims, walls);
+    if (L.d == 3) {
+      wx = wall_diff(u, 2, 1, p, dims, walls) - wall_diff(u, 1, 2, p, dims, walls);
+      wy = wall_diff(u, 0, 2, p, dims, walls) - wall_diff(u, 2, 0, p, dims, walls);
+    }
+    s += wgt * 0.5 * (wx * wx + wy * wy + wz * wz);
+  }
+  free(rho);
+  free(u);
+  free(pi);
   *out = s;
   return 0;
 }

@@ -15,6 +15,13 @@ Workloads (lattice units, c_s^2 = 1/3, nu = c_s^2 (tau - 1/2)):
   * ``taylor_green_3d``   u = U0 (sin x cos y cos z, -cos x sin y cos z, 0) on
                           [0, 2 pi)^3 at cell centres, rho = 1 + U0^2/(16 c_s^2)
                           (cos 2x + cos 2y)(cos 2z + 2), optional phase shift.
+  * ``dipole_2d``         the dipole of the dipole-wall benchmark (Sec. 4.1,
+                          eq_dipole1 / eq_dipole2) on the nodes of [-1, 1]^2
+                          (N intervals per unit length, no-slip walls on the
+                          boundary nodes), velocities scaled by U_lb.
+  * ``channel_wave``      u_x = U sin(pi y / (ny - 1)) between no-slip walls on
+                          the first and last y planes, the slowest decaying
+                          Stokes mode of the channel.
   * ``random_field``      rho = 1 + a_rho * N(0,1), u = a_u * N(0,1), seeded:
                           a field with every Fourier mode present, for parity
                           tests that must exercise all index paths.
@@ -87,6 +94,61 @@ def taylor_green_3d_tau(n: int, mach: float = 0.1, re: float = 1600.0) -> float:
     u0 = mach * math.sqrt(CS2)
     nu = u0 * (n / (2.0 * math.pi)) / re
     return 0.5 + nu / CS2
+
+
+# Dipole-wall benchmark (Sec. 4.1): core vorticity, monopole radius and
+# centres printed in the paper; Re = L U / nu = 2500 with L = 1 (half width).
+DIPOLE_OMEGA_E = 299.5286
+DIPOLE_R0 = 0.1
+DIPOLE_CENTRES = ((0.0, 0.1), (0.0, -0.1))
+DIPOLE_RE = 2500.0
+
+
+def dipole_velocity(x, y):
+    """Dimensionless dipole velocity (u_x, u_y) at points (x, y) (eq_dipole1,
+    eq_dipole2): monopole 1 (positive core vorticity) at (0, 0.1), monopole 2
+    (negative) at (0, -0.1)."""
+    (x1, y1), (x2, y2) = DIPOLE_CENTRES
+    we, r0 = DIPOLE_OMEGA_E, DIPOLE_R0
+    e1 = np.exp(-((x - x1) ** 2 + (y - y1) ** 2) / r0 ** 2)
+    e2 = np.exp(-((x - x2) ** 2 + (y - y2) ** 2) / r0 ** 2)
+    ux = -0.5 * we * (y - y1) * e1 + 0.5 * we * (y - y2) * e2
+    uy = 0.5 * we * (x - x1) * e1 - 0.5 * we * (x - x2) * e2
+    return ux, uy
+
+
+def dipole_2d(N: int, u_lb: float | None = None):
+    """Nodes x_i = -1 + i / N, i = 0 .. 2N, in both directions (the wall nodes
+    lie on x, y = +-1); rho = 1 and u = U_lb * (dipole velocity), zero on the
+    wall nodes. U_lb defaults to 0.01 * 125 / N (the paper's convergence series
+    at constant nu)."""
+    u_lb = dipole_u_lb(N) if u_lb is None else u_lb
+    n = 2 * N + 1
+    X = -1.0 + np.arange(n) / N
+    x, y = np.meshgrid(X, X, indexing="xy")
+    ux, uy = dipole_velocity(x, y)
+    u = np.zeros((2, 1, n, n))
+    u[0, 0], u[1, 0] = u_lb * ux, u_lb * uy
+    u[:, 0, 0, :] = u[:, 0, -1, :] = u[:, 0, :, 0] = u[:, 0, :, -1] = 0.0
+    return np.ones((1, n, n)), u
+
+
+def dipole_u_lb(N: int) -> float:
+    return 0.01 * 125.0 / N
+
+
+def dipole_tau(N: int, u_lb: float | None = None) -> float:
+    u_lb = dipole_u_lb(N) if u_lb is None else u_lb
+    return 0.5 + (u_lb * N / DIPOLE_RE) / CS2
+
+
+def channel_wave(nx: int, ny: int, nz: int, u0: float, dims: int = 2):
+    """u_x = u0 sin(pi y / (ny - 1)) on nodes y = 0 .. ny - 1 (zero on both wall
+    planes), rho = 1."""
+    y = np.arange(ny)
+    u = np.zeros((dims, nz, ny, nx))
+    u[0] = u0 * np.sin(np.pi * y / (ny - 1))[None, :, None]
+    return np.ones((nz, ny, nx)), u
 
 
 def random_field(shape, dims: int, seed: int, a_rho: float = 0.01, a_u: float = 0.05):
