@@ -75,20 +75,41 @@ typedef struct lb_options {
   int lattice;    /* LB_D2Q9 or LB_D3Q27 */
   int nx, ny, nz; /* grid size in cells, each >= 1; nz == 1 for D2Q9 */
   double tau;     /* shifted relaxation time tau-bar > 1/2 (Sec. 3.3) */
-  int periodic;   /* must be 1: every face is periodic */
+  int periodic;   /* must be 1: every face without a wall is periodic */
   int storage;    /* LB_STORE_* */
   int collision;  /* LB_COLLIDE_* */
+  int walls;      /* LB_WALL_* mask: no-slip walls through the first and last
+                     node planes of these axes (each >= 3 nodes), 0 = none */
 } lb_options;
+
+/* No-slip walls (Sec. 3.5, boundary conditions): the boundary nodes lie on
+ * the walls and carry u = 0; each is closed by the regularized Dirichlet
+ * procedure in its zero-velocity form (an unknown population, one that would
+ * stream in from outside, takes the value of its opposite, so rho and
+ * Pi^(1) follow from the lattice symmetries; a buried link of an edge or
+ * corner is set to equilibrium) and then relaxed to f0(rho, 0) +
+ * (1 - 1/tau) f1(Pi^(1)) whatever the collision model. lb_moments and
+ * lb_diagnostics report these closed states (u = 0 on the walls);
+ * lb_enstrophy uses second-order one-sided differences on the wall planes and
+ * the trapezoidal rule (weight 1/2 per wall plane a node lies on);
+ * lb_init_fields starts wall nodes at rest. Populations that stream in from
+ * outside are undefined in lb_get_populations. The learned closure and
+ * lb_coarsen need periodic contexts; lb_diagnostics_static assumes one. */
+#define LB_WALL_X 1
+#define LB_WALL_Y 2
+#define LB_WALL_Z 4
 
 /* Create a context holding one device population store of Q*nx*ny*nz values
  * (AA pattern: one buffer, updated in place) on the current CUDA device. The
  * populations start at rest (f = w, rho = 1, u = 0). Storage F32, model RR.
  * Returns LB_EINVAL for a bad lattice, a size < 1, nz != 1 with D2Q9,
- * tau <= 1/2 or periodic != 1; LB_ENOMEM if the store does not fit.
+ * tau <= 1/2 or periodic != 1; LB_ENOMEM if the store does not fit. No walls.
  * Sec. 3.2 (q populations per node), Sec. 3.3 (tau). */
 LB_API int lb_create(lb_ctx **out, int lattice, int nx, int ny, int nz, double tau, int periodic);
 
-/* As lb_create, with the storage precision and collision model chosen. */
+/* As lb_create, with the storage precision, collision model and walls
+ * chosen; LB_EINVAL also for a walls mask outside the lattice's axes or a
+ * walled axis with fewer than 3 nodes. */
 LB_API int lb_create_ex(lb_ctx **out, const lb_options *opt);
 
 /* Free the context and its device memory. NULL is accepted. */

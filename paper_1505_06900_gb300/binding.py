@@ -20,6 +20,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED = 0, 1, 2, 3, 4
 D2Q9, D3Q27 = 9, 27
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 COLLIDE_RR, COLLIDE_REG2, COLLIDE_BGK = 0, 1, 2
+WALL_X, WALL_Y, WALL_Z = 1, 2, 4
 INIT_EQ, INIT_EQ_NEQ_FD = 0, 1
 
 # every entry point of include/lbrr.h with its ctypes signature
@@ -65,7 +66,7 @@ LB_STATIC_MAX_CELLS = 134217728
 
 class LBOptions(ctypes.Structure):
     _fields_ = [("lattice", _i), ("nx", _i), ("ny", _i), ("nz", _i), ("tau", _d),
-                ("periodic", _i), ("storage", _i), ("collision", _i)]
+                ("periodic", _i), ("storage", _i), ("collision", _i), ("walls", _i)]
 
 
 class LBError(RuntimeError):
@@ -114,7 +115,7 @@ class Solver:
     """One lattice Boltzmann context (device population store) of liblbrr.so."""
 
     def __init__(self, lattice: int, shape, tau: float, storage: int = STORE_F32,
-                 collision: int = COLLIDE_RR, stream=None):
+                 collision: int = COLLIDE_RR, stream=None, walls: int = 0):
         import torch
         self._lib = load()
         self.lattice = lattice
@@ -122,7 +123,9 @@ class Solver:
         self.nx, self.ny, self.nz = (list(shape) + [1])[:3] if len(shape) == 2 else shape
         self.n = self.nx * self.ny * self.nz
         self.tau = float(tau)
-        opt = LBOptions(lattice, self.nx, self.ny, self.nz, self.tau, 1, storage, collision)
+        self.walls = int(walls)
+        opt = LBOptions(lattice, self.nx, self.ny, self.nz, self.tau, 1, storage, collision,
+                        self.walls)
         h = ctypes.c_void_p()
         rc = self._lib.lb_create_ex(ctypes.byref(h), ctypes.addressof(opt))
         if rc != LB_OK:
@@ -169,10 +172,13 @@ class Solver:
     # -- the method -------------------------------------------------------
     def init_fields(self, rho, u, mode: int = INIT_EQ_NEQ_FD):
         """rho [nz,ny,nx] and u [D,nz,ny,nx] float32 CUDA tensors."""
+        import torch
         rho = rho.contiguous()
         u = u.contiguous()
         assert rho.numel() == self.n and u.numel() == self.d * self.n
-        assert rho.is_cuda and u.is_cuda and rho.dtype == u.dtype
+        assert rho.is_cuda and u.is_cuda
+        if rho.dtype != torch.float32 or u.dtype != torch.float32:
+            raise TypeError("rho and u must be float32 CUDA tensors")
         self._check(self._lib.lb_init_fields(self._h, _ptr(rho), _ptr(u), int(mode)))
         self._keep = (rho, u)  # keep alive until the stream has consumed them
 

@@ -164,7 +164,18 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
     return fail(nullptr, LB_EINVAL, "ny and nz must be <= 65535");
   if (!(opt->tau > 0.5) || !std::isfinite(opt->tau))
     return fail(nullptr, LB_EINVAL, "tau must be a finite number > 1/2 (got %g)", opt->tau);
-  if (opt->periodic != 1) return fail(nullptr, LB_EINVAL, "only fully periodic grids are supported");
+  if (opt->periodic != 1)
+    return fail(nullptr, LB_EINVAL, "periodic must be 1 (the faces without walls are periodic)");
+  const int dims = lat == LB_D2Q9 ? 2 : 3;
+  if (opt->walls < 0 || opt->walls >= (1 << dims))
+    return fail(nullptr, LB_EINVAL, "walls must be a mask of the %d axes (got %d)", dims,
+                opt->walls);
+  {
+    const int sz[3] = {opt->nx, opt->ny, opt->nz};
+    for (int a = 0; a < dims; ++a)
+      if (((opt->walls >> a) & 1) && sz[a] < 3)
+        return fail(nullptr, LB_EINVAL, "a walled axis needs at least 3 nodes");
+  }
   if (opt->storage < LB_STORE_F32 || opt->storage > LB_STORE_BF16)
     return fail(nullptr, LB_EINVAL, "unknown storage %d", opt->storage);
   if (opt->collision != LB_COLLIDE_RR && opt->collision != LB_COLLIDE_REG2 &&
@@ -178,7 +189,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   c->lattice = lat;
   c->q = lat;
   c->d = lat == LB_D2Q9 ? 2 : 3;
-  c->g = lbrr::Grid{opt->nx, opt->ny, opt->nz, n};
+  c->g = lbrr::Grid{opt->nx, opt->ny, opt->nz, n, opt->walls};
   c->tau = opt->tau;
   c->storage = opt->storage;
   c->collision = opt->collision;
@@ -214,7 +225,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
 }
 
 int lb_create(lb_ctx **out, int lattice, int nx, int ny, int nz, double tau, int periodic) {
-  lb_options o{lattice, nx, ny, nz, tau, periodic, LB_STORE_F32, LB_COLLIDE_RR};
+  lb_options o{lattice, nx, ny, nz, tau, periodic, LB_STORE_F32, LB_COLLIDE_RR, 0};
   return lb_create_ex(out, &o);
 }
 
@@ -614,8 +625,9 @@ static int ensure_mom(lb_ctx *c) {
 }
 
 static int closure_capable(lb_ctx *c) {
-  if (c->lattice != LB_D3Q27 || c->storage != LB_STORE_F32 || c->collision != LB_COLLIDE_RR)
-    return fail(c, LB_EINVAL, "the learned closure needs a D3Q27, FP32, RR context");
+  if (c->lattice != LB_D3Q27 || c->storage != LB_STORE_F32 || c->collision != LB_COLLIDE_RR ||
+      c->g.walls)
+    return fail(c, LB_EINVAL, "the learned closure needs a periodic D3Q27, FP32, RR context");
   return LB_OK;
 }
 
@@ -647,8 +659,8 @@ int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
   LB_CHECK_CTX(fine);
   LB_CHECK_CTX(coarse);
   if (fine->lattice != LB_D3Q27 || coarse->lattice != LB_D3Q27 || fine->storage != LB_STORE_F32 ||
-      coarse->storage != LB_STORE_F32)
-    return fail(coarse, LB_EINVAL, "coarsening needs two D3Q27 FP32 contexts");
+      coarse->storage != LB_STORE_F32 || fine->g.walls || coarse->g.walls)
+    return fail(coarse, LB_EINVAL, "coarsening needs two periodic D3Q27 FP32 contexts");
   if (fine->g.nx != 2 * coarse->g.nx || fine->g.ny != 2 * coarse->g.ny ||
       fine->g.nz != 2 * coarse->g.nz)
     return fail(coarse, LB_EINVAL, "the fine grid must be twice the coarse grid in every direction");

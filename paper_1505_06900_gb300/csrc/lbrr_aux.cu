@@ -34,7 +34,13 @@ __global__ void __launch_bounds__(kAuxThreads)
   m.jy = m.rho * m.uy;
   m.jz = m.rho * m.uz;
   m.pxx = m.pxy = m.pxz = m.pyy = m.pyz = m.pzz = 0.0f;
-  if (mode == 1) {
+  // nodes on a wall start at rest, f = f0(rho, 0)
+  const bool wall = g.walls && unknown_mask<Q>(g, x, y, z) != 0;
+  if (wall) {
+    m.ux = m.uy = m.uz = 0.0f;
+    m.jx = m.jy = m.jz = 0.0f;
+  }
+  if (mode == 1 && !wall) {
     // du[b][a] = d u_b / d x_a by periodic central differences
     float du[3][3] = {};
     const int p[3] = {x, y, z};
@@ -104,7 +110,11 @@ __global__ void __launch_bounds__(kAuxThreads)
   cell_coords(cell, g, x, y, z);
   float df[Q];
   load_logical<Q, S>(f, g, parity, x, y, z, df);
-  const Macro m = Lattice<Q>::moments(df);
+  // a node on a wall reports its closed state (rho of the fill, u = 0)
+  const uint32_t unknown = g.walls ? unknown_mask<Q>(g, x, y, z) : 0u;
+  if (unknown) wall_fill<Q>(unknown, df);
+  Macro m = Lattice<Q>::moments(df);
+  if (unknown) wall_macro(m);
   const long long n = g.n;
   if (rho) rho[cell] = m.rho;
   if (u) {
@@ -200,7 +210,10 @@ __global__ void __launch_bounds__(kRedThreads)
         const int xs = cx < 0 ? xm : (cx > 0 ? xp : x);
         df[i] = Storage<S>::template load<D>(f + srow[sl] + xs, i);
       }
-      const Macro m = Lattice<Q>::moments(df);
+      const uint32_t unknown = g.walls ? unknown_mask<Q>(g, x, r % g.ny, r / g.ny) : 0u;
+      if (unknown) wall_fill<Q>(unknown, df);
+      Macro m = Lattice<Q>::moments(df);
+      if (unknown) wall_macro(m);
       part[0] += m.drho;
       part[1] += m.jx;
       part[2] += m.jy;
@@ -248,26 +261,41 @@ __global__ void __launch_bounds__(kRedThreads)
        cell += stride) {
     int x, y, z;
     cell_coords(cell, g, x, y, z);
-    auto at = [&](int comp, int xx, int yy, int zz) -> double {
-      return (double)u[comp * n + ((long long)zz * g.ny + yy) * g.nx + xx];
+    const int p[3] = {x, y, z}, dims[3] = {g.nx, g.ny, g.nz};
+    // d u_comp / d x_axis: central differences (periodic across periodic
+    // faces); second-order one-sided on the wall planes of a walled axis
+    auto diff = [&](int comp, int axis) -> double {
+      int q[3] = {p[0], p[1], p[2]};
+      auto at = [&](int k) -> double {
+        q[axis] = k;
+        return (double)u[comp * n + ((long long)q[2] * g.ny + q[1]) * g.nx + q[0]];
+      };
+      const int a = p[axis], m = dims[axis];
+      if ((g.walls >> axis) & 1) {
+        if (a == 0) {
+          const double u0 = at(0), u1 = at(1), u2 = at(2);
+          return 0.5 * (-3.0 * u0 + 4.0 * u1 - u2);
+        }
+        if (a == m - 1) {
+          const double u0 = at(m - 1), u1 = at(m - 2), u2 = at(m - 3);
+          return 0.5 * (3.0 * u0 - 4.0 * u1 + u2);
+        }
+      }
+      const double up = at(a + 1 == m ? 0 : a + 1);
+      const double um = at(a == 0 ? m - 1 : a - 1);
+      return 0.5 * (up - um);
     };
-    const int xp = wrap_add(x, 1, g.nx), xm = wrap_add(x, -1, g.nx);
-    const int yp = wrap_add(y, 1, g.ny), ym = wrap_add(y, -1, g.ny);
-    // d_a u_b = (u_b(x + e_a) - u_b(x - e_a)) / 2
-    const double dxuy = 0.5 * (at(1, xp, y, z) - at(1, xm, y, z));
-    const double dyux = 0.5 * (at(0, x, yp, z) - at(0, x, ym, z));
-    const double wz = dxuy - dyux;
+    double wgt = 1.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (((g.walls >> a) & 1) && (p[a] == 0 || p[a] == dims[a] - 1)) wgt *= 0.5;
+    const double wz = diff(1, 0) - diff(0, 1);
     double wx = 0.0, wy = 0.0;
     if (D == 3) {
-      const int zp = wrap_add(z, 1, g.nz), zm = wrap_add(z, -1, g.nz);
-      const double dyuz = 0.5 * (at(2, x, yp, z) - at(2, x, ym, z));
-      const double dzuy = 0.5 * (at(1, x, y, zp) - at(1, x, y, zm));
-      const double dzux = 0.5 * (at(0, x, y, zp) - at(0, x, y, zm));
-      const double dxuz = 0.5 * (at(2, xp, y, z) - at(2, xm, y, z));
-      wx = dyuz - dzuy;
-      wy = dzux - dxuz;
+      wx = diff(2, 1) - diff(1, 2);
+      wy = diff(0, 2) - diff(2, 0);
     }
-    acc[0] += 0.5 * (wx * wx + wy * wy + wz * wz);
+    acc[0] += wgt * 0.5 * (wx * wx + wy * wy + wz * wz);
   }
   block_sum<1>(acc, partials + blockIdx.x);
 }

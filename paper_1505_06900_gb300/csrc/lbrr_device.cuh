@@ -400,10 +400,13 @@ __host__ __device__ constexpr int vel(int i, int a) {
   return a == 0 ? i % 3 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1);
 }
 
-// Grid geometry passed by value to every kernel.
+// Grid geometry passed by value to every kernel. walls: bit a set = axis a
+// is bounded by no-slip walls through its first and last node planes
+// (Sec. 3.5, boundary conditions); other axes are periodic.
 struct Grid {
   int nx, ny, nz;
   long long n;  // nx * ny * nz (cells per population slot)
+  int walls = 0;
 };
 
 // Periodic neighbour coordinate c + d, d in {-1, 0, 1}.
@@ -411,6 +414,87 @@ __device__ __forceinline__ int wrap_add(int c, int d, int n) {
   int r = c + d;
   r = (r < 0) ? r + n : r;
   return (r >= n) ? r - n : r;
+}
+
+// ---------------------------------------------------------------- walls --
+// Populations whose velocity component along axis a equals s (+1 or -1).
+template <int Q>
+__host__ __device__ constexpr uint32_t vel_mask(int a, int s) {
+  uint32_t m = 0;
+  for (int i = 0; i < Q; ++i)
+    if (vel(i, a) == s) m |= 1u << i;
+  return m;
+}
+
+// Populations of node (x, y, z) that stream in from outside the domain
+// (x - xi_i beyond a wall plane): c_a = +1 on the first plane of a walled
+// axis a, c_a = -1 on the last. Zero off the walls.
+template <int Q>
+__device__ __forceinline__ uint32_t unknown_mask(const Grid &g, int x, int y, int z) {
+  constexpr int D = Lattice<Q>::D;
+  uint32_t m = 0;
+  if (g.walls & 1) {
+    if (x == 0) m |= vel_mask<Q>(0, 1);
+    if (x == g.nx - 1) m |= vel_mask<Q>(0, -1);
+  }
+  if (g.walls & 2) {
+    if (y == 0) m |= vel_mask<Q>(1, 1);
+    if (y == g.ny - 1) m |= vel_mask<Q>(1, -1);
+  }
+  if (D == 3 && (g.walls & 4)) {
+    if (z == 0) m |= vel_mask<Q>(2, 1);
+    if (z == g.nz - 1) m |= vel_mask<Q>(2, -1);
+  }
+  return m;
+}
+
+// bit i set <-> bit opp(i) = Q - 1 - i of m set
+template <int Q>
+__device__ __forceinline__ uint32_t opposite_mask(uint32_t m) {
+  return __brev(m) >> (32 - Q);
+}
+
+// Zero-velocity no-slip closure of a boundary node (the regularized
+// Dirichlet procedure of Sec. 3.5 with u_bc = 0), on shifted populations:
+// with u_bc = 0 the equilibrium is the same for a population and its
+// opposite, so giving an unknown population the value of its known opposite
+// is the off-equilibrium bounce-back from which the lattice symmetries give
+// rho and Pi^(1). A buried link (population and opposite both unknown) is
+// set to equilibrium, w_i (rho - 1), with rho closing the mass balance.
+template <int Q>
+__device__ __forceinline__ void wall_fill(uint32_t unknown, float (&df)[Q]) {
+  constexpr int D = Lattice<Q>::D;
+  const uint32_t buried = unknown & opposite_mask<Q>(unknown);
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (((unknown & ~buried) >> i) & 1u) df[i] = df[Q - 1 - i];
+  if (buried) {
+    float s = 0.f, wb = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if ((buried >> i) & 1u)
+        wb += weight<D>(i);
+      else
+        s += df[i];
+    }
+    const float drho = s / (1.f - wb);
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      if ((buried >> i) & 1u) df[i] = weight<D>(i) * drho;
+  }
+}
+
+// Impose u = u_bc = 0 on the moments of a filled boundary node: Pi^(1) is
+// then sum xi xi df - c_s^2 (rho - 1) I without the rho u u term.
+__device__ __forceinline__ void wall_macro(Macro &m) {
+  m.pxx += m.jx * m.ux;
+  m.pyy += m.jy * m.uy;
+  m.pzz += m.jz * m.uz;
+  m.pxy += m.jx * m.uy;
+  m.pxz += m.jx * m.uz;
+  m.pyz += m.jy * m.uz;
+  m.jx = m.jy = m.jz = 0.f;
+  m.ux = m.uy = m.uz = 0.f;
 }
 
 // Logical (natural-order, pre-collision) shifted populations of cell (x, y, z)

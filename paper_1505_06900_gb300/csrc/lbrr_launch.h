@@ -20,6 +20,11 @@ constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3,
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
                         int parity, int *status, cudaStream_t st);
 
+// The update of a grid with no-slip walls (g.walls != 0; lbrr_walls.cu),
+// any storage; launch_step dispatches to it.
+cudaError_t launch_step_walls(int q, int storage, int model, void *f, const Grid &g, float om1,
+                              int parity, cudaStream_t st);
+
 // The persistent row kernel for 16-bit stores (lbrr_step16.cu): sets
 // launched = false, launching nothing, where it does not apply (nx not a
 // multiple of 16, nx < 64, nx above 1024 (D3Q27) or 2048 (D2Q9), or no
@@ -53,7 +58,9 @@ cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g,
                                double *partials, double *out, cudaStream_t st);
 
 // 0.5 sum |curl u|^2 from a velocity field u [D][N] (central differences),
-// reduced through partials [kRedBlocks] into out[0].
+// reduced through partials [kRedBlocks] into out[0]. With walls: second-order
+// one-sided differences on the wall planes and the trapezoidal weights (1/2
+// per wall plane a node lies on).
 cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
                              cudaStream_t st);
 

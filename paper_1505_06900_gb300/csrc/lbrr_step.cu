@@ -108,6 +108,7 @@ static cudaError_t step_s(int storage, int model, void *f, const Grid &g, float 
 
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
                         int parity, int *status, cudaStream_t st) {
+  if (g.walls) return launch_step_walls(q, storage, model, f, g, om1, parity, st);
   // 16-bit stores: row segments of 128 cells where nx allows (the fastest),
   // else whole rows, else one thread per cell
   if (storage != 0) {

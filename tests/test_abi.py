@@ -65,6 +65,20 @@ def test_create_ex_rejects_bad_options(lib):
     assert lib.lb_create_ex(None, ctypes.addressof(o)) == B.LB_EINVAL
 
 
+@pytest.mark.parametrize("opts,fragment", [
+    ((9, 8, 8, 1, 0.7, 1, 0, 0, 4), "walls"),        # z walls on a 2D lattice
+    ((27, 8, 8, 8, 0.7, 1, 0, 0, 8), "walls"),       # no fourth axis
+    ((27, 8, 8, 8, 0.7, 1, 0, 0, -1), "walls"),
+    ((9, 8, 2, 1, 0.7, 1, 0, 0, 2), "at least 3"),  # walled axis too short
+])
+def test_create_ex_rejects_bad_walls(lib, opts, fragment):
+    h = ctypes.c_void_p()
+    o = B.LBOptions(*opts)
+    assert lib.lb_create_ex(ctypes.byref(h), ctypes.addressof(o)) == B.LB_EINVAL
+    assert not h.value
+    assert fragment in lib.lb_last_error(None).decode()
+
+
 def test_null_context_is_rejected(lib):
     assert lib.lb_step(None, 1) == B.LB_EINVAL
     assert lib.lb_moments(None, None, None, None) == B.LB_EINVAL
