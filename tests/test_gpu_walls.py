@@ -145,3 +145,15 @@ def test_dipole_enstrophy_peaks_match_the_paper(N, tol):
     ref1, ref2 = golden["enstrophy_peaks"]
     assert 0.3 < p1["t"] < 0.36 and abs(p1["enstrophy"] / ref1 - 1.0) < tol
     assert 0.55 < p2["t"] < 0.7 and abs(p2["enstrophy"] / ref2 - 1.0) < tol
+
+
+def test_dipole_at_mach_0_7_stays_stable_with_rr_only():
+    """Sec. 4.1 runs the dipole at a peak Mach number of 0.7 (U_lb = 0.032,
+    Re = 2500) with the recursive model; the order-2 regularized model of
+    Sec. 3.6.1, whose shear modes the paper finds unstable at high velocity,
+    blows up on the same run."""
+    r = dipole.run(250, t_end=0.75, u_lb=0.032)
+    assert all(np.isfinite(p["enstrophy"]) for p in r["peaks"])
+    assert abs(r["peaks"][0]["enstrophy"] / 3313.0 - 1.0) < 0.2
+    with pytest.raises(B.LBError):
+        dipole.run(250, t_end=0.75, u_lb=0.032, collision=B.COLLIDE_REG2)
