@@ -27,6 +27,8 @@ struct lb_ctx {
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
   float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
   float *ystd = nullptr;       // lazily allocated 17 * n floats: the network's predictions
+  void *xs = nullptr;          // feature source of the TMA-fed network (row-tile grids)
+  CUtensorMap xs_map{};        // its tensor map
   const lb_mlp *closure = nullptr;  // learned closure in use (not owned)
   float closure_bound = 0.f;
   unsigned long long *fallbacks = nullptr;  // device counter of cells that fell back to RR
@@ -93,6 +95,8 @@ int free_all(lb_ctx *c) {
   if (c->fields) cudaFree(c->fields);
   if (c->mom) cudaFree(c->mom);
   if (c->ystd) cudaFree(c->ystd);
+  if (c->xs) cudaFree(c->xs);
+  c->xs = nullptr;
   if (c->fallbacks) cudaFree(c->fallbacks);
   c->mom = nullptr;
   c->ystd = nullptr;
@@ -266,7 +270,17 @@ int lb_step(lb_ctx *c, int n) {
   const float om1 = (float)(1.0 - 1.0 / c->tau);
   for (int k = 0; k < n; ++k) {
     cudaError_t e;
-    if (c->closure) {
+    if (c->closure && c->xs) {
+      e = lbrr::launch_feature_source(c->closure->d, static_cast<const float *>(c->f), c->g,
+                                      c->parity, c->xs, c->stream);
+      if (e == cudaSuccess)
+        e = lbrr::launch_mlp_conv(c->closure->d, c->xs_map, c->g, c->ystd, c->closure->status,
+                                  c->closure->nblocks, c->stream);
+      if (e == cudaSuccess)
+        e = lbrr::launch_step_delta(c->closure->d, static_cast<float *>(c->f), c->g, om1,
+                                    c->parity, c->ystd, c->fallbacks, c->closure_bound,
+                                    c->stream);
+    } else if (c->closure) {
       e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
       if (e == cudaSuccess)
         e = lbrr::launch_mlp_tc(c->closure->d, nullptr, c->mom, &c->g, c->g.n, c->ystd,
@@ -612,11 +626,25 @@ int lb_mlp_train_step(lb_mlp *m, const void *X, const float *T, long long M, flo
   return mlp_backward(m, X, T, M, nullptr, 1, lr, loss);
 }
 
-static int ensure_mom(lb_ctx *c) {
-  if (c->mom && c->ystd) return LB_OK;
+// Closure scratch: the moment field (features of lb_closure_features and the
+// network of grids that are not whole row tiles), the predictions, and for
+// row-tile grids the feature source of the TMA-fed network with its map.
+static int ensure_mom(lb_ctx *c, bool for_step) {
+  const bool conv = for_step && lbrr::mlp_conv_supported(c->g);
   cudaError_t e = cudaSuccess;
-  if (!c->mom) e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
+  if (!conv && !c->mom) e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
   if (e == cudaSuccess && !c->ystd) e = cudaMalloc(&c->ystd, sizeof(float) * 17 * (size_t)c->g.n);
+  if (e == cudaSuccess && conv && !c->xs) {
+    e = cudaMalloc(&c->xs, lbrr::feature_source_bytes(c->g));
+    if (e == cudaSuccess) {
+      e = lbrr::make_feature_map(c->xs, c->g, &c->xs_map);
+      if (e != cudaSuccess) {
+        cudaFree(c->xs);
+        c->xs = nullptr;
+        return fail(c, LB_ECUDA, "cannot encode the feature-source tensor map");
+      }
+    }
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, LB_ENOMEM, "cannot allocate the closure fields");
@@ -635,7 +663,7 @@ int lb_closure_features(lb_ctx *c, const lb_mlp *m, void *X) {
   LB_CHECK_CTX(c);
   if (!m || !X) return fail(c, LB_EINVAL, "null argument");
   int rc = closure_capable(c);
-  if (rc == LB_OK) rc = ensure_mom(c);
+  if (rc == LB_OK) rc = ensure_mom(c, false);
   if (rc != LB_OK) return rc;
   DeviceGuard dg(c->device);
   cudaError_t e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
@@ -685,7 +713,7 @@ int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
   }
   if (!(bound > 0.f)) return fail(c, LB_EINVAL, "bound must be positive");
   int rc = closure_capable(c);
-  if (rc == LB_OK) rc = ensure_mom(c);
+  if (rc == LB_OK) rc = ensure_mom(c, true);
   if (rc != LB_OK) return rc;
   DeviceGuard dg(c->device);
   if (!c->fallbacks) {

@@ -2,6 +2,7 @@
 // target extraction, coarsening, the closure step). Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -71,6 +72,17 @@ cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int pa
 // [M][32]. *status becomes 1 if a tensor-core wait timed out.
 cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, const Grid *g,
                           long long M, float *Y, int *status, int nblocks, cudaStream_t st);
+// The TMA-fed, pipelined forward pass (lbrr_mlp_conv.cu) for grids whose
+// rows are whole 128-cell tiles: the feature source xs (standardised moments,
+// BF16, 16 channels, one-cell periodic halo: feature_source_bytes(g) bytes),
+// its tensor map, and the network on it writing Y [17][N].
+bool mlp_conv_supported(const Grid &g);
+size_t feature_source_bytes(const Grid &g);
+cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map);
+cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid &g, int parity,
+                                  void *xs, cudaStream_t st);
+cudaError_t launch_mlp_conv(const MlpDevice &p, const CUtensorMap &map, const Grid &g, float *Y,
+                            int *status, int nblocks, cudaStream_t st);
 // One update of an FP32 D3Q27 store with the learned correction: ystd [17][N]
 // holds the network's standardised predictions for the current populations.
 cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,

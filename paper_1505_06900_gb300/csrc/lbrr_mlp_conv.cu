@@ -1,0 +1,451 @@
+// Closure-network forward pass for grids whose rows are whole 128-cell tiles,
+// fed by the tensor memory accelerator (TMA) and pipelined across tiles.
+//
+// Layer 1 of the network is a 3x3x3 convolution of the standardised moment
+// field: its 270 inputs for a cell are the 10 moments of the 27 cells around
+// it. A feature-source tensor holds those moments once per cell, standardised
+// and rounded to BF16, channels-last with 16 channels (10 used) and a one-cell
+// periodic halo: xs[z + 1][y + 1][x + 1][16]. For a tile of 128 cells
+// x0 .. x0 + 127 of row (y, z) the kernel copies, per neighbour row
+// (y + dy, z + dz), the 130 positions x0 - 1 .. x0 + 128 with two TMA tile
+// loads (channels 0-7 and 8-15), which lands them as [130 rows][16 bytes]:
+// the canonical K-major layout without swizzle (8-row groups 128 bytes
+// apart, the two channel halves one row block apart). The 27 MMAs of layer
+// 1 (M 128, N 64, K 16, one per neighbour (dx, dy, dz)) read that block
+// starting dx + 1 rows in; the weight operand of each neighbour is W1's 10
+// columns of that neighbour, zero-padded to 16.
+//
+// One persistent block per SM, ten warps:
+//   warp 0      TMA producer: 18 tile loads per tile into one of 3 stages
+//   warp 1      layer-1 MMA issuer (and TMEM owner), accumulators double-
+//               buffered across tiles (TMEM columns 0-63, 64-127)
+//   warps 2-5,  two epilogue groups taking alternate tiles; each reads its
+//   warps 6-9   layer-1 accumulator (thread = TMEM lane = tile row), applies
+//               bias and tanh, writes the BF16 hidden row, issues layers 2
+//               and 3 itself (columns 128 + 64 g, 256 + 32 g) and writes the
+//               17 standardised outputs of its row.
+// Stages, accumulators and epilogue groups are handed over with mbarriers;
+// every wait is bounded. On a timeout the block raises a shared abort flag,
+// every role leaves its loop, copies and MMAs still in flight are waited for
+// (bounded), the tensor memory is freed and *status is set to 1.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+
+#include "lbrr_launch.h"
+#include "lbrr_mlp.h"
+#include "lbrr_mma.cuh"
+#include "lbrr_tc.cuh"
+
+namespace lbrr {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kCRows = 128;                         // cells per tile
+constexpr int kCSpan = kCRows + 2;                  // staged positions x0 - 1 .. x0 + 128
+constexpr uint32_t kHalfBytes = kCSpan * 16;        // one channel half of a neighbour row
+constexpr uint32_t kHalfPitch = 2176;               // the same, 128-byte aligned
+constexpr uint32_t kStageBytes = 18 * kHalfPitch;   // 9 neighbour rows x 2 halves
+constexpr uint32_t kTxBytes = 18 * kHalfBytes;      // bytes a stage receives
+constexpr int kStages = 3;
+constexpr int kTaps = 27;
+constexpr uint32_t kTapBytes = 2 * kMlpHidden * 16;  // W1 block of one neighbour
+constexpr uint32_t kA2Bytes = kCRows * kMlpHidden * 2;
+constexpr int kConvThreads = 320;
+constexpr uint32_t kTmemCols = 512;
+
+constexpr uint32_t kOffW1 = 0;
+constexpr uint32_t kOffW2 = kOffW1 + kTaps * kTapBytes;
+constexpr uint32_t kOffW3 = kOffW2 + kMlpHidden * kMlpHidden * 2;
+constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
+constexpr uint32_t kOffA2 = kOffA1 + kStages * kStageBytes;
+constexpr uint32_t kOffMisc = kOffA2 + 2 * kA2Bytes;
+constexpr uint32_t kConvSmem = kOffMisc + 1024;
+static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfPitch % 128 == 0,
+              "TMA destinations are 128-byte aligned");
+static_assert(kConvSmem <= 232448, "fits the shared memory of one block");
+
+// mbarriers in the misc area
+enum : int {
+  kBarFull = 0,    // [3] stage loaded (TMA transaction bytes)
+  kBarEmpty = 3,   // [3] stage consumed by the layer-1 MMAs (tcgen05.commit)
+  kBarAcc1F = 6,   // [2] layer-1 accumulator ready (tcgen05.commit)
+  kBarAcc1E = 8,   // [2] layer-1 accumulator read by its epilogue group
+  kBarL2 = 10,     // [2] layer 2 done
+  kBarL3 = 12,     // [2] layer 3 done
+  kBarDrain = 14,  // [3] drain of each MMA issuer after an abort
+  kNumBars = 17
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+// 4-D tiled TMA load (coordinates innermost first), completing on mbar
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      : "memory");
+}
+// barrier of one epilogue group (4 warps, named barrier 1 + g)
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g) : "memory");
+}
+// the same, returning whether any thread of the group passed pred = true
+__device__ __forceinline__ bool group_any(int g, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, 128, p;\n"
+      "selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+// tanh(acc + bias) of the 64 accumulator columns in v into row r of a K = 64
+// operand (canonical layout), BF16
+__device__ __forceinline__ void hidden_row(const uint32_t (&v)[64], const float *bias,
+                                           unsigned char *dst, int r) {
+#pragma unroll
+  for (int k = 0; k < 64; k += 8) {
+    uint4 q;
+    q.x = pack_bf16(tanh_approx(__uint_as_float(v[k]) + bias[k]),
+                    tanh_approx(__uint_as_float(v[k + 1]) + bias[k + 1]));
+    q.y = pack_bf16(tanh_approx(__uint_as_float(v[k + 2]) + bias[k + 2]),
+                    tanh_approx(__uint_as_float(v[k + 3]) + bias[k + 3]));
+    q.z = pack_bf16(tanh_approx(__uint_as_float(v[k + 4]) + bias[k + 4]),
+                    tanh_approx(__uint_as_float(v[k + 5]) + bias[k + 5]));
+    q.w = pack_bf16(tanh_approx(__uint_as_float(v[k + 6]) + bias[k + 6]),
+                    tanh_approx(__uint_as_float(v[k + 7]) + bias[k + 7]));
+    *reinterpret_cast<uint4 *>(dst + cm_offset(r, k, kMlpHidden)) = q;
+  }
+}
+
+__device__ __forceinline__ void load_acc64(uint32_t taddr, uint32_t (&v)[64]) {
+  uint32_t (&a)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[0]);
+  uint32_t (&b)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[16]);
+  uint32_t (&c)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[32]);
+  uint32_t (&d)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[48]);
+  tmem_ld16_async(taddr, a);
+  tmem_ld16_async(taddr + 16, b);
+  tmem_ld16_async(taddr + 32, c);
+  tmem_ld16_async(taddr + 48, d);
+  tmem_wait_ld();
+}
+
+__global__ void __launch_bounds__(kConvThreads, 1)
+    mlp_conv_kernel(MlpDevice p, const __grid_constant__ CUtensorMap xs_map, const Grid g,
+                    float *__restrict__ Y, int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc + kNumBars * 8);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+  int *counts = reinterpret_cast<int *>(tmem_slot + 2);  // loads issued, stages landed
+  float *sb = reinterpret_cast<float *>(smem + kOffMisc + 256);  // b1, b2, b3
+  auto bar = [&](int k) -> uint32_t { return smem_u32(bars + k); };
+
+  // ---- weights (canonical layouts) and biases
+  for (int q = tid; q < kTaps * 2 * kMlpHidden; q += kConvThreads) {
+    const int tap = q / (2 * kMlpHidden), rem = q - tap * 2 * kMlpHidden;
+    const int h = rem / kMlpHidden, n = rem - h * kMlpHidden;
+    uint32_t w[4];
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+      const int k0 = 8 * h + c;
+      const __nv_bfloat16 *src = p.w1 + n * kMlpIn + kMlpMoments * tap + k0;
+      const uint16_t lo = k0 < kMlpMoments ? __bfloat16_as_ushort(src[0]) : 0;
+      const uint16_t hi = k0 + 1 < kMlpMoments ? __bfloat16_as_ushort(src[1]) : 0;
+      w[c / 2] = (uint32_t)lo | ((uint32_t)hi << 16);
+    }
+    *reinterpret_cast<uint4 *>(smem + kOffW1 + tap * kTapBytes + h * 1024 + n * 16) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int c = tid; c < kMlpHidden * (kMlpHidden / 8); c += kConvThreads) {
+    const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
+    *reinterpret_cast<uint4 *>(smem + kOffW2 + cm_offset(n, 8 * kb, kMlpHidden)) =
+        *reinterpret_cast<const uint4 *>(p.w2 + n * kMlpHidden + 8 * kb);
+  }
+  for (int c = tid; c < kMlpOut * (kMlpHidden / 8); c += kConvThreads) {
+    const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
+    *reinterpret_cast<uint4 *>(smem + kOffW3 + cm_offset(n, 8 * kb, kMlpHidden)) =
+        *reinterpret_cast<const uint4 *>(p.w3 + n * kMlpHidden + 8 * kb);
+  }
+  for (int c = tid; c < 2 * kMlpHidden + kMlpOut; c += kConvThreads)
+    sb[c] = c < kMlpHidden ? p.b1[c] : (c < 2 * kMlpHidden ? p.b2[c - kMlpHidden]
+                                                           : p.b3[c - 2 * kMlpHidden]);
+  if (tid == 0) {
+    for (int k = 0; k < kNumBars; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(k)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *abort_flag = 0;
+    counts[0] = counts[1] = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long ntiles = g.n / kCRows;
+  const uint32_t sw1 = smem_u32(smem + kOffW1), sw2 = smem_u32(smem + kOffW2);
+  const uint32_t sw3 = smem_u32(smem + kOffW3), sa1 = smem_u32(smem + kOffA1);
+
+  if (warp == 0) {
+    // ---------------------------------------------------------- producer
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&xs_map))
+                   : "memory");
+      int issued = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (*abort_flag) break;
+        const int s = issued % kStages, use = issued / kStages;
+        if (!mbar_wait(bar(kBarEmpty + s), (use & 1) ^ 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(bar(kBarFull + s), kTxBytes);
+        const long long first = tile * kCRows;
+        const int x0 = (int)(first % g.nx);
+        const long long yz = first / g.nx;
+        const int y = (int)(yz % g.ny), z = (int)(yz / g.ny);
+#pragma unroll 1
+        for (int r9 = 0; r9 < 9; ++r9) {
+          const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            tma_load_4d(sa1 + s * kStageBytes + (2 * r9 + h) * kHalfPitch, &xs_map, 8 * h, x0,
+                        y + dy + 1, z + dz + 1, bar(kBarFull + s));
+        }
+        ++issued;
+      }
+      counts[0] = issued;
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------- layer-1 MMA issuer
+    if (lane == 0) {
+      int landed = 0;
+      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (*abort_flag) break;
+        const int j = landed, s = j % kStages, gs = j & 1;
+        if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        ++landed;
+        if (!mbar_wait(bar(kBarAcc1E + gs), ((j >> 1) & 1) ^ 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+#pragma unroll 1
+        for (int tap = 0; tap < kTaps; ++tap) {
+          const int dx = tap % 3 - 1, r9 = tap / 3;
+          const uint64_t a = sdesc(sa1 + s * kStageBytes + 2 * r9 * kHalfPitch + (dx + 1) * 16,
+                                   kHalfPitch, 128);
+          const uint64_t b = sdesc(sw1 + tap * kTapBytes, 1024, 128);
+          umma(tmem + 64 * gs, a, b, idesc_bf16(kCRows, kMlpHidden), tap > 0);
+        }
+        umma_commit(bar(kBarEmpty + s));
+        umma_commit(bar(kBarAcc1F + gs));
+      }
+      counts[1] = landed;
+    }
+  } else {
+    // --------------------------------------------------- epilogue groups
+    const int eg = (warp - 2) >> 2;
+    const int quarter = warp & 3;               // TMEM lanes 32 quarter .. (warp % 4 rule)
+    const int r = 32 * quarter + lane;          // tile row
+    const bool leader = warp == 2 + 4 * eg && lane == 0;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
+    unsigned char *a2 = smem + kOffA2 + eg * kA2Bytes;
+    const uint32_t sa2 = smem_u32(a2);
+    uint32_t ph2 = 0, ph3 = 0;
+    int j = eg;
+    for (long long tile = blockIdx.x + (long long)eg * gridDim.x; tile < ntiles;
+         tile += 2LL * gridDim.x, j += 2) {
+      bool ok = mbar_wait(bar(kBarAcc1F + eg), (j >> 1) & 1);
+      if (group_any(eg, !ok || *abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      uint32_t v[64];
+      load_acc64(lane_addr + 64 * eg, v);
+      fence_before();
+      group_sync(eg);
+      if (leader) mbar_arrive(bar(kBarAcc1E + eg));
+      // layer 1 epilogue -> layer 2
+      hidden_row(v, sb, a2, r);
+      fence_async_smem();
+      group_sync(eg);
+      if (leader) {
+        fence_after();
+#pragma unroll
+        for (int ks = 0; ks < kMlpHidden / 16; ++ks)
+          umma(tmem + 128 + 64 * eg, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+               sdesc(sw2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+               idesc_bf16(kCRows, kMlpHidden), ks > 0);
+        umma_commit(bar(kBarL2 + eg));
+      }
+      ok = mbar_wait(bar(kBarL2 + eg), ph2);
+      ph2 ^= 1;
+      if (group_any(eg, !ok)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      load_acc64(lane_addr + 128 + 64 * eg, v);
+      // layer 2 epilogue -> layer 3 (the layer-2 operand has been read)
+      hidden_row(v, sb + kMlpHidden, a2, r);
+      fence_async_smem();
+      fence_before();
+      group_sync(eg);
+      if (leader) {
+        fence_after();
+#pragma unroll
+        for (int ks = 0; ks < kMlpHidden / 16; ++ks)
+          umma(tmem + 256 + 32 * eg, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+               sdesc(sw3 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(kCRows, kMlpOut),
+               ks > 0);
+        umma_commit(bar(kBarL3 + eg));
+      }
+      ok = mbar_wait(bar(kBarL3 + eg), ph3);
+      ph3 ^= 1;
+      if (group_any(eg, !ok)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      uint32_t y[32];
+      uint32_t (&y0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&y[0]);
+      uint32_t (&y1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&y[16]);
+      tmem_ld16_async(lane_addr + 256 + 32 * eg, y0);
+      tmem_ld16_async(lane_addr + 256 + 32 * eg + 16, y1);
+      tmem_wait_ld();
+      fence_before();
+      const long long cell = tile * kCRows + r;
+      const float *b3 = sb + 2 * kMlpHidden;
+#pragma unroll
+      for (int k = 0; k < kMlpOutUsed; ++k) Y[k * g.n + cell] = __uint_as_float(y[k]) + b3[k];
+    }
+  }
+
+  __syncthreads();
+  if (*abort_flag) {
+    // copies and MMAs still in flight land before the memory goes away
+    if (tid == 0) {
+      atomicExch(status, 1);
+      for (int k = counts[1]; k < counts[0]; ++k)
+        mbar_wait(bar(kBarFull + k % kStages), (k / kStages) & 1);
+    }
+    const bool issuer = (warp == 1 && lane == 0) || ((warp == 2 || warp == 6) && lane == 0);
+    if (issuer) {
+      const int d = warp == 1 ? 0 : (warp == 2 ? 1 : 2);
+      umma_commit(bar(kBarDrain + d));
+      mbar_wait(bar(kBarDrain + d), 0);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+}
+
+// Feature source: standardised moments (BF16, 16 channels) of every cell of
+// the periodically padded grid, from the logical populations of an FP32 store.
+// The same moments and rounding as the features of lb_closure_features.
+__global__ void __launch_bounds__(256)
+    feature_source_kernel(MlpDevice p, const float *__restrict__ f, const Grid g, const int parity,
+                          uint4 *__restrict__ xs) {
+  const long long px = g.nx + 2, py = g.ny + 2, pz = g.nz + 2;
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= px * py * pz) return;
+  const int X = (int)(q % px);
+  const long long t = q / px;
+  const int Yp = (int)(t % py), Z = (int)(t / py);
+  const int x = X == 0 ? g.nx - 1 : (X == g.nx + 1 ? 0 : X - 1);
+  const int y = Yp == 0 ? g.ny - 1 : (Yp == g.ny + 1 ? 0 : Yp - 1);
+  const int z = Z == 0 ? g.nz - 1 : (Z == g.nz + 1 ? 0 : Z - 1);
+  float df[27];
+  load_logical<27, 0>(f, g, parity, x, y, z, df);
+  const Macro m = Lattice<27>::moments(df);
+  const float v[kMlpMoments] = {m.drho, m.ux, m.uy, m.uz, m.pxx, m.pxy, m.pxz, m.pyy, m.pyz, m.pzz};
+  uint32_t w[5];
+#pragma unroll
+  for (int k = 0; k < kMlpMoments; k += 2)
+    w[k / 2] = pack_bf16((v[k] - p.in_mean[k]) * p.in_inv_std[k],
+                         (v[k + 1] - p.in_mean[k + 1]) * p.in_inv_std[k + 1]);
+  xs[2 * q] = make_uint4(w[0], w[1], w[2], w[3]);
+  xs[2 * q + 1] = make_uint4(w[4], 0u, 0u, 0u);
+}
+
+}  // namespace
+
+bool mlp_conv_supported(const Grid &g) { return g.nx % kCRows == 0 && g.walls == 0; }
+
+size_t feature_source_bytes(const Grid &g) {
+  return (size_t)(g.nx + 2) * (size_t)(g.ny + 2) * (size_t)(g.nz + 2) * 32;
+}
+
+cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {16, (cuuint64_t)g.nx + 2, (cuuint64_t)g.ny + 2,
+                              (cuuint64_t)g.nz + 2};
+  const cuuint64_t strides[3] = {32, 32 * dims[1], 32 * dims[1] * dims[2]};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kCSpan, 1, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xs, dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid &g, int parity,
+                                  void *xs, cudaStream_t st) {
+  const long long cells = (long long)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+  feature_source_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(
+      p, f, g, parity, static_cast<uint4 *>(xs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_conv(const MlpDevice &p, const CUtensorMap &map, const Grid &g, float *Y,
+                            int *status, int nblocks, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(mlp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kConvSmem);
+  if (e != cudaSuccess) return e;
+  const long long tiles = g.n / kCRows;
+  const int nb = (int)(tiles < nblocks ? tiles : nblocks);
+  if (nb < 1) return cudaSuccess;
+  mlp_conv_kernel<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, Y, status);
+  return cudaGetLastError();
+}
+
+}  // namespace lbrr

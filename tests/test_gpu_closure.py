@@ -182,7 +182,11 @@ def _closure_case(seed, out_scale_value, shape=(64 + 16, 3, 4)):
 # (Every extent is >= 3: with 2 cells along an axis the periodic central
 # difference vanishes, a moment kind has zero variance and its
 # standardisation amplifies round-off.)
-@pytest.mark.parametrize("shape", [(80, 3, 4), (128, 3, 3)])
+# (80, 3, 4): rows that are not whole 128-cell tiles (network fed by threads);
+# (128, 3, 3) and (256, 16, 16): row tiles, the TMA-fed pipelined network, the
+# latter with 512 tiles, so blocks take several tiles (stage and accumulator
+# reuse, both epilogue groups)
+@pytest.mark.parametrize("shape", [(80, 3, 4), (128, 3, 3), (256, 16, 16)])
 def test_closure_step_matches_oracle_and_zero_network_is_rr(shape):
     """Two closure updates against the reference with the network evaluated at
     the kernels' precision (BF16 features and hidden layers)."""
