@@ -15,15 +15,18 @@
 // starting dx + 1 rows in; the weight operand of each neighbour is W1's 10
 // columns of that neighbour, zero-padded to 16.
 //
-// One persistent block per SM, ten warps:
-//   warp 0      TMA producer: 18 tile loads per tile into one of 3 stages
-//   warp 1      layer-1 MMA issuer (and TMEM owner), accumulators double-
-//               buffered across tiles (TMEM columns 0-63, 64-127)
-//   warps 2-5,  two epilogue groups taking alternate tiles; each reads its
-//   warps 6-9   layer-1 accumulator (thread = TMEM lane = tile row), applies
-//               bias and tanh, writes the BF16 hidden row, issues layers 2
-//               and 3 itself (columns 128 + 64 g, 256 + 32 g) and writes the
-//               17 standardised outputs of its row.
+// One persistent block per SM, eighteen warps:
+//   warp 0      TMA producer: 18 tile loads per tile into one of 2 stages
+//   warp 1      layer-1 MMA issuer (and TMEM owner)
+//   warps 2-17  four epilogue groups of four warps taking every fourth tile;
+//               each reads its layer-1 accumulator (thread = TMEM lane = tile
+//               row), applies bias and tanh, writes the BF16 hidden row,
+//               issues layers 2 and 3 itself and writes the 17 standardised
+//               outputs of its row.
+// Group g owns TMEM columns 128 g .. 128 g + 127: the first 64 take its
+// layer-1 accumulator (released as soon as the group has read it, so the
+// next tile's layer 1 can start), the other 64 its layer 2 and then layer 3.
+// Every barrier is waited on by one role in the order of its phases.
 // Stages, accumulators and epilogue groups are handed over with mbarriers;
 // every wait is bounded. On a timeout the block raises a shared abort flag,
 // every role leaves its loop, copies and MMAs still in flight are waited for
@@ -50,11 +53,12 @@ constexpr uint32_t kHalfBytes = kCSpan * 16;        // one channel half of a nei
 constexpr uint32_t kHalfPitch = 2176;               // the same, 128-byte aligned
 constexpr uint32_t kStageBytes = 18 * kHalfPitch;   // 9 neighbour rows x 2 halves
 constexpr uint32_t kTxBytes = 18 * kHalfBytes;      // bytes a stage receives
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kTaps = 27;
 constexpr uint32_t kTapBytes = 2 * kMlpHidden * 16;  // W1 block of one neighbour
 constexpr uint32_t kA2Bytes = kCRows * kMlpHidden * 2;
-constexpr int kConvThreads = 320;
+constexpr int kGroups = 4;                          // epilogue groups
+constexpr int kConvThreads = 32 * (2 + 4 * kGroups);
 constexpr uint32_t kTmemCols = 512;
 
 constexpr uint32_t kOffW1 = 0;
@@ -62,7 +66,7 @@ constexpr uint32_t kOffW2 = kOffW1 + kTaps * kTapBytes;
 constexpr uint32_t kOffW3 = kOffW2 + kMlpHidden * kMlpHidden * 2;
 constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
 constexpr uint32_t kOffA2 = kOffA1 + kStages * kStageBytes;
-constexpr uint32_t kOffMisc = kOffA2 + 2 * kA2Bytes;
+constexpr uint32_t kOffMisc = kOffA2 + kGroups * kA2Bytes;
 constexpr uint32_t kConvSmem = kOffMisc + 1024;
 static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfPitch % 128 == 0,
               "TMA destinations are 128-byte aligned");
@@ -70,15 +74,16 @@ static_assert(kConvSmem <= 232448, "fits the shared memory of one block");
 
 // mbarriers in the misc area
 enum : int {
-  kBarFull = 0,    // [3] stage loaded (TMA transaction bytes)
-  kBarEmpty = 3,   // [3] stage consumed by the layer-1 MMAs (tcgen05.commit)
-  kBarAcc1F = 6,   // [2] layer-1 accumulator ready (tcgen05.commit)
-  kBarAcc1E = 8,   // [2] layer-1 accumulator read by its epilogue group
-  kBarL2 = 10,     // [2] layer 2 done
-  kBarL3 = 12,     // [2] layer 3 done
-  kBarDrain = 14,  // [3] drain of each MMA issuer after an abort
-  kNumBars = 17
+  kBarFull = 0,                       // [stages] stage loaded (TMA transaction bytes)
+  kBarEmpty = kBarFull + kStages,     // [stages] stage consumed by the layer-1 MMAs
+  kBarAcc1F = kBarEmpty + kStages,    // [groups] layer-1 accumulator ready (tcgen05.commit)
+  kBarAcc1E = kBarAcc1F + kGroups,    // [groups] layer-1 accumulator read by its group
+  kBarL2 = kBarAcc1E + kGroups,       // [groups] layer 2 done
+  kBarL3 = kBarL2 + kGroups,          // [groups] layer 3 done
+  kBarDrain = kBarL3 + kGroups,       // [1 + groups] drain of each MMA issuer after an abort
+  kNumBars = kBarDrain + 1 + kGroups
 };
+static_assert(kNumBars * 8 + 16 <= 256, "barriers, TMEM slot and counters before the biases");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
@@ -112,34 +117,30 @@ __device__ __forceinline__ bool group_any(int g, bool pred) {
   return r != 0;
 }
 
-// tanh(acc + bias) of the 64 accumulator columns in v into row r of a K = 64
-// operand (canonical layout), BF16
-__device__ __forceinline__ void hidden_row(const uint32_t (&v)[64], const float *bias,
-                                           unsigned char *dst, int r) {
+// tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v) into row r
+// of a K = 64 operand (canonical layout), BF16
+__device__ __forceinline__ void hidden_half(const uint32_t (&v)[32], const float *bias, int c0,
+                                            unsigned char *dst, int r) {
 #pragma unroll
-  for (int k = 0; k < 64; k += 8) {
+  for (int k = 0; k < 32; k += 8) {
     uint4 q;
-    q.x = pack_bf16(tanh_approx(__uint_as_float(v[k]) + bias[k]),
-                    tanh_approx(__uint_as_float(v[k + 1]) + bias[k + 1]));
-    q.y = pack_bf16(tanh_approx(__uint_as_float(v[k + 2]) + bias[k + 2]),
-                    tanh_approx(__uint_as_float(v[k + 3]) + bias[k + 3]));
-    q.z = pack_bf16(tanh_approx(__uint_as_float(v[k + 4]) + bias[k + 4]),
-                    tanh_approx(__uint_as_float(v[k + 5]) + bias[k + 5]));
-    q.w = pack_bf16(tanh_approx(__uint_as_float(v[k + 6]) + bias[k + 6]),
-                    tanh_approx(__uint_as_float(v[k + 7]) + bias[k + 7]));
-    *reinterpret_cast<uint4 *>(dst + cm_offset(r, k, kMlpHidden)) = q;
+    q.x = pack_bf16(tanh_approx(__uint_as_float(v[k]) + bias[c0 + k]),
+                    tanh_approx(__uint_as_float(v[k + 1]) + bias[c0 + k + 1]));
+    q.y = pack_bf16(tanh_approx(__uint_as_float(v[k + 2]) + bias[c0 + k + 2]),
+                    tanh_approx(__uint_as_float(v[k + 3]) + bias[c0 + k + 3]));
+    q.z = pack_bf16(tanh_approx(__uint_as_float(v[k + 4]) + bias[c0 + k + 4]),
+                    tanh_approx(__uint_as_float(v[k + 5]) + bias[c0 + k + 5]));
+    q.w = pack_bf16(tanh_approx(__uint_as_float(v[k + 6]) + bias[c0 + k + 6]),
+                    tanh_approx(__uint_as_float(v[k + 7]) + bias[c0 + k + 7]));
+    *reinterpret_cast<uint4 *>(dst + cm_offset(r, c0 + k, kMlpHidden)) = q;
   }
 }
 
-__device__ __forceinline__ void load_acc64(uint32_t taddr, uint32_t (&v)[64]) {
+__device__ __forceinline__ void load_acc32(uint32_t taddr, uint32_t (&v)[32]) {
   uint32_t (&a)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[0]);
   uint32_t (&b)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[16]);
-  uint32_t (&c)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[32]);
-  uint32_t (&d)[16] = *reinterpret_cast<uint32_t(*)[16]>(&v[48]);
   tmem_ld16_async(taddr, a);
   tmem_ld16_async(taddr + 16, b);
-  tmem_ld16_async(taddr + 32, c);
-  tmem_ld16_async(taddr + 48, d);
   tmem_wait_ld();
 }
 
@@ -221,10 +222,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
           break;
         }
         mbar_expect_tx(bar(kBarFull + s), kTxBytes);
-        const long long first = tile * kCRows;
-        const int x0 = (int)(first % g.nx);
-        const long long yz = first / g.nx;
-        const int y = (int)(yz % g.ny), z = (int)(yz / g.ny);
+        // tile -> (x0, y, z) in 32-bit arithmetic (the launcher keeps the
+        // tile count below 2^31)
+        const uint32_t t = (uint32_t)tile, tpr = (uint32_t)g.nx / kCRows;
+        const uint32_t row = t / tpr;
+        const int x0 = (int)(t - row * tpr) * kCRows;
+        const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
 #pragma unroll 1
         for (int r9 = 0; r9 < 9; ++r9) {
           const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
@@ -243,24 +246,27 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       int landed = 0;
       for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (*abort_flag) break;
-        const int j = landed, s = j % kStages, gs = j & 1;
+        const int j = landed, s = j % kStages, gs = j % kGroups;
         if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1)) {
           *abort_flag = 1;
           break;
         }
         ++landed;
-        if (!mbar_wait(bar(kBarAcc1E + gs), ((j >> 1) & 1) ^ 1)) {
+        if (!mbar_wait(bar(kBarAcc1E + gs), ((j / kGroups) & 1) ^ 1)) {
           *abort_flag = 1;
           break;
         }
         fence_after();
-#pragma unroll 1
+        // descriptors of tap 0; a tap adds its byte offset / 16 to the start
+        // address field (no carry: shared addresses stay below 256 KB)
+        const uint64_t a0 = sdesc(sa1 + s * kStageBytes, kHalfPitch, 128);
+        const uint64_t b0 = sdesc(sw1, 1024, 128);
+        const uint32_t d = tmem + 128 * gs;
+#pragma unroll
         for (int tap = 0; tap < kTaps; ++tap) {
-          const int dx = tap % 3 - 1, r9 = tap / 3;
-          const uint64_t a = sdesc(sa1 + s * kStageBytes + 2 * r9 * kHalfPitch + (dx + 1) * 16,
-                                   kHalfPitch, 128);
-          const uint64_t b = sdesc(sw1 + tap * kTapBytes, 1024, 128);
-          umma(tmem + 64 * gs, a, b, idesc_bf16(kCRows, kMlpHidden), tap > 0);
+          const uint32_t aoff = 2 * (tap / 3) * kHalfPitch + (tap % 3) * 16;
+          umma(d, a0 + (aoff >> 4), b0 + ((tap * kTapBytes) >> 4),
+               idesc_bf16(kCRows, kMlpHidden), tap > 0);
         }
         umma_commit(bar(kBarEmpty + s));
         umma_commit(bar(kBarAcc1F + gs));
@@ -269,37 +275,40 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     }
   } else {
     // --------------------------------------------------- epilogue groups
-    const int eg = (warp - 2) >> 2;
+    const int eg = (warp - 2) >> 2;             // group 0 .. kGroups - 1
     const int quarter = warp & 3;               // TMEM lanes 32 quarter .. (warp % 4 rule)
     const int r = 32 * quarter + lane;          // tile row
     const bool leader = warp == 2 + 4 * eg && lane == 0;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
     unsigned char *a2 = smem + kOffA2 + eg * kA2Bytes;
     const uint32_t sa2 = smem_u32(a2);
+    const uint32_t c1 = 128 * eg, c2 = 128 * eg + 64, c3 = c2;  // layer 1, 2, 3 columns
     uint32_t ph2 = 0, ph3 = 0;
-    int j = eg;
+    int j = eg;  // the block's tile index
     for (long long tile = blockIdx.x + (long long)eg * gridDim.x; tile < ntiles;
-         tile += 2LL * gridDim.x, j += 2) {
-      bool ok = mbar_wait(bar(kBarAcc1F + eg), (j >> 1) & 1);
+         tile += (long long)kGroups * gridDim.x, j += kGroups) {
+      bool ok = mbar_wait(bar(kBarAcc1F + eg), (j / kGroups) & 1);
       if (group_any(eg, !ok || *abort_flag)) {
         *abort_flag = 1;
         break;
       }
       fence_after();
-      uint32_t v[64];
-      load_acc64(lane_addr + 64 * eg, v);
+      uint32_t v[32];
+      // layer 1 epilogue (hidden row 1), releasing the accumulator once read
+      load_acc32(lane_addr + c1, v);
+      hidden_half(v, sb, 0, a2, r);
+      load_acc32(lane_addr + c1 + 32, v);
       fence_before();
       group_sync(eg);
       if (leader) mbar_arrive(bar(kBarAcc1E + eg));
-      // layer 1 epilogue -> layer 2
-      hidden_row(v, sb, a2, r);
+      hidden_half(v, sb, 32, a2, r);
       fence_async_smem();
       group_sync(eg);
       if (leader) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-          umma(tmem + 128 + 64 * eg, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+          umma(tmem + c2, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
                sdesc(sw2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
                idesc_bf16(kCRows, kMlpHidden), ks > 0);
         umma_commit(bar(kBarL2 + eg));
@@ -311,9 +320,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         break;
       }
       fence_after();
-      load_acc64(lane_addr + 128 + 64 * eg, v);
-      // layer 2 epilogue -> layer 3 (the layer-2 operand has been read)
-      hidden_row(v, sb + kMlpHidden, a2, r);
+      // layer 2 epilogue (hidden row 2 over row 1, which layer 2 has read)
+      load_acc32(lane_addr + c2, v);
+      hidden_half(v, sb + kMlpHidden, 0, a2, r);
+      load_acc32(lane_addr + c2 + 32, v);
+      hidden_half(v, sb + kMlpHidden, 32, a2, r);
       fence_async_smem();
       fence_before();
       group_sync(eg);
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-          umma(tmem + 256 + 32 * eg, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+          umma(tmem + c3, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
                sdesc(sw3 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(kCRows, kMlpOut),
                ks > 0);
         umma_commit(bar(kBarL3 + eg));
@@ -333,17 +344,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         break;
       }
       fence_after();
-      uint32_t y[32];
-      uint32_t (&y0)[16] = *reinterpret_cast<uint32_t(*)[16]>(&y[0]);
-      uint32_t (&y1)[16] = *reinterpret_cast<uint32_t(*)[16]>(&y[16]);
-      tmem_ld16_async(lane_addr + 256 + 32 * eg, y0);
-      tmem_ld16_async(lane_addr + 256 + 32 * eg + 16, y1);
-      tmem_wait_ld();
+      load_acc32(lane_addr + c3, v);
       fence_before();
       const long long cell = tile * kCRows + r;
       const float *b3 = sb + 2 * kMlpHidden;
 #pragma unroll
-      for (int k = 0; k < kMlpOutUsed; ++k) Y[k * g.n + cell] = __uint_as_float(y[k]) + b3[k];
+      for (int k = 0; k < kMlpOutUsed; ++k) Y[k * g.n + cell] = __uint_as_float(v[k]) + b3[k];
     }
   }
 
@@ -355,9 +361,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       for (int k = counts[1]; k < counts[0]; ++k)
         mbar_wait(bar(kBarFull + k % kStages), (k / kStages) & 1);
     }
-    const bool issuer = (warp == 1 && lane == 0) || ((warp == 2 || warp == 6) && lane == 0);
-    if (issuer) {
-      const int d = warp == 1 ? 0 : (warp == 2 ? 1 : 2);
+    const bool lead = warp >= 2 && ((warp - 2) & 3) == 0 && lane == 0;
+    if ((warp == 1 && lane == 0) || lead) {
+      const int d = warp == 1 ? 0 : 1 + ((warp - 2) >> 2);
       umma_commit(bar(kBarDrain + d));
       mbar_wait(bar(kBarDrain + d), 0);
     }
@@ -442,6 +448,7 @@ cudaError_t launch_mlp_conv(const MlpDevice &p, const CUtensorMap &map, const Gr
                                        (int)kConvSmem);
   if (e != cudaSuccess) return e;
   const long long tiles = g.n / kCRows;
+  if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
   const int nb = (int)(tiles < nblocks ? tiles : nblocks);
   if (nb < 1) return cudaSuccess;
   mlp_conv_kernel<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, Y, status);
