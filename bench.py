@@ -283,6 +283,21 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
     }
 
 
+def dipole_variant(B, N: int = 500):
+    """The dipole-wall collision (walls, D2Q9, Re 2500) at N = 500 with each
+    storage precision: the two enstrophy maxima against the reference values
+    the paper prints, i.e. the error each store reaches on a physical
+    benchmark, and the update rate (enstrophy sampling included)."""
+    from paper_1505_06900_gb300 import dipole
+    out = {"N": N, "nodes": (2 * N + 1) ** 2, "reference": list(dipole.REFERENCE_PEAKS)}
+    for name, st in (("f32", B.STORE_F32), ("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
+        r = dipole.run(N, t_end=0.75, storage=st)
+        out[name] = {"glups": r["glups"], "steps": r["steps"],
+                     "peaks": [p["enstrophy"] for p in r["peaks"]],
+                     "errors": [p["error"] for p in r["peaks"]]}
+    return out
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -340,6 +355,7 @@ def run_gpu(args):
     del u_f32
     variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
                                           sync_all, main["total_ms"] / args.steps)
+    variants["dipole_wall"] = dipole_variant(B)
 
     # end to end through host buffers (pinned), one lb_run_host call of K steps
     rho_h = torch.from_numpy(rho32).pin_memory()
