@@ -48,6 +48,7 @@ extern "C" {
 #define LB_ENOMEM 2    /* a device or host allocation failed */
 #define LB_ECUDA 3     /* a CUDA call or kernel launch failed */
 #define LB_EDIVERGED 4 /* a diagnostic is not finite: the run has blown up */
+#define LB_ETIMEOUT 5  /* a bounded wait inside a kernel expired (its results are incomplete) */
 
 /* lattices */
 #define LB_D2Q9 9
@@ -131,7 +132,7 @@ LB_API int lb_init_fields(lb_ctx *ctx, const float *rho, const float *u, int ini
 /* Advance n >= 0 full collide-and-stream updates (eq_discr_bgk_reg). n == 0 is
  * a no-op. Asynchronous on the context's stream. With a 16-bit store the
  * update waits (boundedly) for its own bulk copies; if such a wait ever
- * expires, the next lb_diagnostics or lb_get_state returns LB_ECUDA. */
+ * expires, the next lb_diagnostics or lb_get_state returns LB_ETIMEOUT. */
 LB_API int lb_step(lb_ctx *ctx, int n);
 
 /* Macroscopic fields of the current populations into device buffers:
@@ -226,7 +227,8 @@ LB_API int lb_mlp_get_params(lb_mlp *mlp, float *params);
  * in_inv_std and out_scale must be finite and non-zero). */
 LB_API int lb_mlp_set_scaling(lb_mlp *mlp, const float *in_mean, const float *in_inv_std,
                               const float *out_scale);
-/* Y [M][32] (device, FP32) = network(X [M][288], device, BF16). */
+/* Y [M][32] (device, FP32) = network(X [M][288], device, BF16). Synchronises;
+ * LB_ETIMEOUT if a bounded tensor-core wait of the network kernel expired. */
 LB_API int lb_mlp_forward(lb_mlp *mlp, const void *X, long long M, float *Y);
 /* Gradient of the loss over the batch into grad [LB_MLP_PARAMS] (device) and
  * the loss into *loss (host, may be NULL); parameters unchanged. Deterministic. */
@@ -249,7 +251,9 @@ LB_API int lb_coarsen(lb_ctx *fine, lb_ctx *coarse);
  * not all positive, takes the RR update instead and is counted. The network
  * must outlive its use. */
 LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
-/* Cells that fell back to RR since the closure was first set (host out). */
+/* Cells that fell back to RR since the closure was first set (host out).
+ * Synchronises; LB_ETIMEOUT if a bounded tensor-core wait of the closure's
+ * network ever expired in lb_step. */
 LB_API int lb_closure_fallbacks(lb_ctx *ctx, long long *count);
 
 /* Largest grid (nx * ny * nz cells) that lb_diagnostics_static accepts. */

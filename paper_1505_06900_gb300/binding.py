@@ -16,7 +16,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "liblbrr.so")
 
-LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED = 0, 1, 2, 3, 4
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED, LB_ETIMEOUT = 0, 1, 2, 3, 4, 5
 D2Q9, D3Q27 = 9, 27
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 COLLIDE_RR, COLLIDE_REG2, COLLIDE_BGK = 0, 1, 2

@@ -132,7 +132,7 @@ int diagnostics(lb_ctx *c, double *out) {
     e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics copy");
-  if (st) return fail(c, LB_ECUDA, "a bulk-copy wait of the 16-bit step kernel timed out");
+  if (st) return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
   out[0] = (double)c->g.n + h[0];
   for (int a = 0; a < c->d; ++a) out[1 + a] = h[1 + a];
   out[1 + c->d] = h[4];
@@ -371,7 +371,7 @@ int lb_get_state(lb_ctx *c, void *dst, int *parity) {
     e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
-  if (st) return fail(c, LB_ECUDA, "a bulk-copy wait of the 16-bit step kernel timed out");
+  if (st) return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
   *parity = c->parity;
   return LB_OK;
 }
@@ -537,13 +537,13 @@ int lb_mlp_set_params(lb_mlp *m, const float *params) {
   return LB_OK;
 }
 
-// LB_ECUDA if a tensor-core wait of the network ever timed out (synchronises).
+// LB_ETIMEOUT if a tensor-core wait of the network ever timed out (synchronises).
 static int mlp_status(lb_mlp *m, cudaStream_t st) {
   int h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "status: %s", cudaGetErrorString(e));
-  if (h) return mlp_fail(m, LB_ECUDA, "a tensor-core wait of the network timed out");
+  if (h) return mlp_fail(m, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
   return LB_OK;
 }
 
@@ -745,7 +745,7 @@ int lb_closure_fallbacks(lb_ctx *c, long long *count) {
     e = cudaMemcpyAsync(&st, c->closure->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "closure status");
-    if (st) return fail(c, LB_ECUDA, "a tensor-core wait of the network timed out");
+    if (st) return fail(c, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
   }
   return LB_OK;
 }

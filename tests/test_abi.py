@@ -79,6 +79,13 @@ def test_create_ex_rejects_bad_walls(lib, opts, fragment):
     assert fragment in lib.lb_last_error(None).decode()
 
 
+def test_status_codes_match_the_header():
+    text = open(HEADER).read()
+    codes = dict(re.findall(r"^#define (LB_E\w+|LB_OK) (\d+)", text, flags=re.M))
+    for name in ["LB_OK", "LB_EINVAL", "LB_ENOMEM", "LB_ECUDA", "LB_EDIVERGED", "LB_ETIMEOUT"]:
+        assert int(codes[name]) == getattr(B, name), name
+
+
 def test_null_context_is_rejected(lib):
     assert lib.lb_step(None, 1) == B.LB_EINVAL
     assert lib.lb_moments(None, None, None, None) == B.LB_EINVAL
