@@ -256,6 +256,23 @@ LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
  * network ever expired in lb_step. */
 LB_API int lb_closure_fallbacks(lb_ctx *ctx, long long *count);
 
+/* Bounded waits (no counterpart in the paper). Kernels that hand work over
+ * with mbarriers (the 16-bit whole-row step, the closure network) give up a
+ * wait after a fixed number of try-waits, record it in a device status word
+ * and return; the next synchronising call (lb_diagnostics, lb_get_state,
+ * lb_closure_fallbacks, lb_mlp_forward ...) reports LB_ETIMEOUT once and
+ * clears the word. These calls exist to test that path without faulting a
+ * GPU. lb_set_wait_limit / lb_mlp_set_wait_limit set the main-loop limit of
+ * a context's / a network's kernels (iterations >= 1; 0 restores the
+ * default); waits for copies still in flight after a timeout keep the
+ * default. lb_wait_selftest runs one block that waits on an mbarrier nothing
+ * arrives on, for `iterations` >= 1 try-waits, and returns LB_ETIMEOUT when
+ * the expiry was recorded as it must be (LB_ECUDA otherwise); message in
+ * lb_last_error(NULL). */
+LB_API int lb_set_wait_limit(lb_ctx *ctx, int iterations);
+LB_API int lb_mlp_set_wait_limit(lb_mlp *mlp, int iterations);
+LB_API int lb_wait_selftest(int iterations);
+
 /* Largest grid (nx * ny * nz cells) that lb_diagnostics_static accepts. */
 #define LB_STATIC_MAX_CELLS 134217728LL /* 512^3 */
 

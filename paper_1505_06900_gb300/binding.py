@@ -43,6 +43,9 @@ SIGNATURES = {
     "lb_set_state": (_i, [_vp, _vp, _i]),
     "lb_run_host": (_i, [_vp, _vp, _vp, _i, _i, _vp, _vp, _vp]),
     "lb_info": (_i, [_vp, ctypes.POINTER(_ll)]),
+    "lb_set_wait_limit": (_i, [_vp, _i]),
+    "lb_mlp_set_wait_limit": (_i, [_vp, _i]),
+    "lb_wait_selftest": (_i, [_i]),
     "lb_diagnostics_static": (_i, [_i, _i, _i, _i, _i, _i, _vp, _vp, _vp]),
     "lb_mlp_create": (_i, [ctypes.POINTER(_vp)]),
     "lb_mlp_destroy": (None, [_vp]),
@@ -254,6 +257,10 @@ class Solver:
         self._check(self._lib.lb_set_closure(self._h, mlp.handle if mlp else None, float(bound)))
         self._closure = mlp
 
+    def set_wait_limit(self, iterations: int):
+        """Main-loop wait limit of this context's mbarrier kernels (0: default)."""
+        self._check(self._lib.lb_set_wait_limit(self._h, int(iterations)))
+
     def closure_fallbacks(self) -> int:
         out = ctypes.c_longlong()
         self._check(self._lib.lb_closure_fallbacks(self._h, ctypes.byref(out)))
@@ -312,6 +319,10 @@ class MLP:
         self._check(self._lib.lb_mlp_get_params(self._h, p.ctypes.data))
         return p
 
+    def set_wait_limit(self, iterations: int):
+        """Main-loop wait limit of the network kernels (0: default)."""
+        self._check(self._lib.lb_mlp_set_wait_limit(self._h, int(iterations)))
+
     def set_scaling(self, in_mean, in_inv_std, out_scale):
         a = [np.ascontiguousarray(np.asarray(v, dtype=np.float32)) for v in
              (in_mean, in_inv_std, out_scale)]
@@ -344,3 +355,9 @@ class MLP:
                                                 float(lr), ctypes.byref(loss) if want_loss
                                                 else None))
         return loss.value if want_loss else None
+
+
+def wait_selftest(iterations: int = 1000) -> int:
+    """Status code of lb_wait_selftest (LB_ETIMEOUT when the bounded wait
+    expired and was recorded, as it must)."""
+    return int(load().lb_wait_selftest(int(iterations)))

@@ -23,7 +23,8 @@ struct lb_ctx {
   void *f = nullptr;       // population store, q * n elements
   double *partials = nullptr;  // reduction scratch, kRedBlocks * kRedValues doubles
   double *dout = nullptr;      // reduction result, kRedValues doubles
-  int *status = nullptr;       // set to 1 by the 16-bit row kernel if a bounded wait expired
+  int *status = nullptr;       // [0] set to 1 by the 16-bit row kernel if a bounded wait
+                               // expired (cleared when reported), [1] its main-loop wait limit
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
   float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
   float *ystd = nullptr;       // lazily allocated 17 * n floats: the network's predictions
@@ -42,7 +43,8 @@ struct lb_mlp {
   float *gpart = nullptr;      // per-block gradient partials
   float *lpart = nullptr;      // per-block loss partials
   double *dloss = nullptr;
-  int *status = nullptr;       // set to 1 by the tensor-core kernel if a wait timed out
+  int *status = nullptr;       // [0] set to 1 by a tensor-core kernel if a wait timed out
+                               // (cleared when reported), [1] main-loop wait limit (0 default)
   int nblocks = 0;             // blocks of the training kernel (one per SM)
   long long t = 0;             // Adam steps taken
   int device = 0;
@@ -132,7 +134,10 @@ int diagnostics(lb_ctx *c, double *out) {
     e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics copy");
-  if (st) return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
+  if (st) {
+    cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
+  }
   out[0] = (double)c->g.n + h[0];
   for (int a = 0; a < c->d; ++a) out[1 + a] = h[1 + a];
   out[1 + c->d] = h[4];
@@ -208,7 +213,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   if (e == cudaSuccess)
     e = cudaMalloc(&c->partials, sizeof(double) * lbrr::kRedBlocks * lbrr::kRedValues);
   if (e == cudaSuccess) e = cudaMalloc(&c->dout, sizeof(double) * lbrr::kRedValues);
-  if (e == cudaSuccess) e = cudaMalloc(&c->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->status, 2 * sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);
@@ -217,7 +222,7 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   }
   // rest state: df = 0 in every storage precision
   e = cudaMemset(c->f, 0, bytes);
-  if (e == cudaSuccess) e = cudaMemset(c->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->status, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_all(c);
@@ -371,7 +376,10 @@ int lb_get_state(lb_ctx *c, void *dst, int *parity) {
     e = cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
-  if (st) return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
+  if (st) {
+    cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+    return fail(c, LB_ETIMEOUT, "a bulk-copy wait of the 16-bit step kernel timed out");
+  }
   *parity = c->parity;
   return LB_OK;
 }
@@ -486,8 +494,8 @@ int lb_mlp_create(lb_mlp **out) {
   if (e == cudaSuccess) e = cudaMalloc(&m->gpart, 4 * P * (size_t)m->nblocks);
   if (e == cudaSuccess) e = cudaMalloc(&m->lpart, 4 * (size_t)m->nblocks);
   if (e == cudaSuccess) e = cudaMalloc(&m->dloss, sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&m->status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(m->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&m->status, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->status, 0, 2 * sizeof(int));
   if (e != cudaSuccess) {
     cudaGetLastError();
     lb_mlp_destroy(m);
@@ -543,7 +551,10 @@ static int mlp_status(lb_mlp *m, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(&h, m->status, sizeof h, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "status: %s", cudaGetErrorString(e));
-  if (h) return mlp_fail(m, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
+  if (h) {
+    cudaMemsetAsync(m->status, 0, sizeof(int), st);
+    return mlp_fail(m, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
+  }
   return LB_OK;
 }
 
@@ -745,9 +756,54 @@ int lb_closure_fallbacks(lb_ctx *c, long long *count) {
     e = cudaMemcpyAsync(&st, c->closure->status, sizeof st, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "closure status");
-    if (st) return fail(c, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
+    if (st) {
+      cudaMemsetAsync(c->closure->status, 0, sizeof(int), c->stream);
+      return fail(c, LB_ETIMEOUT, "a tensor-core wait of the network timed out");
+    }
   }
   return LB_OK;
+}
+
+// ---------------------------------------------------------- bounded waits
+
+int lb_set_wait_limit(lb_ctx *c, int iterations) {
+  LB_CHECK_CTX(c);
+  if (iterations < 0) return fail(c, LB_EINVAL, "negative wait limit");
+  DeviceGuard dg(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->status + 1, &iterations, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set_wait_limit");
+  return LB_OK;
+}
+
+int lb_mlp_set_wait_limit(lb_mlp *m, int iterations) {
+  if (!m) return LB_EINVAL;
+  if (iterations < 0) return mlp_fail(m, LB_EINVAL, "negative wait limit");
+  DeviceGuard dg(m->device);
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->status + 1, &iterations, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "set_wait_limit: %s", cudaGetErrorString(e));
+  return LB_OK;
+}
+
+int lb_wait_selftest(int iterations) {
+  if (iterations < 1) return lbrr::report_error(LB_EINVAL, "iterations must be >= 1");
+  int *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) e = lbrr::launch_wait_selftest((unsigned)iterations, d, nullptr);
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return lbrr::report_error(LB_ECUDA, "wait self-test: %s", cudaGetErrorString(e));
+  }
+  if (h != 1)
+    return lbrr::report_error(LB_ECUDA, "a wait with no arrival completed (status %d)", h);
+  return lbrr::report_error(LB_ETIMEOUT, "the bounded wait expired and was reported");
 }
 
 }  // extern "C"

@@ -71,6 +71,10 @@ cudaError_t launch_diagnostics_blocks(int q, int storage, const void *f, const G
                                       int parity, int nblocks, double *partials, double *out,
                                       cudaStream_t st);
 
+// One block waiting (bounded, `iterations` try-waits) on an mbarrier nothing
+// arrives on; sets *status to 1 when the wait expires (lbrr_selftest.cu).
+cudaError_t launch_wait_selftest(unsigned iterations, int *status, cudaStream_t st);
+
 // Records a message for lb_last_error(NULL) on the calling thread.
 int report_error(int code, const char *fmt, ...);
 

@@ -28,7 +28,8 @@
 // next tile's layer 1 can start), the other 64 its layer 2 and then layer 3.
 // Every barrier is waited on by one role in the order of its phases.
 // Stages, accumulators and epilogue groups are handed over with mbarriers;
-// every wait is bounded. On a timeout the block raises a shared abort flag,
+// every wait is bounded (status[1] can shorten the main-loop limit to test
+// the timeout path). On a timeout the block raises a shared abort flag,
 // every role leaves its loop, copies and MMAs still in flight are waited for
 // (bounded), the tensor memory is freed and *status is set to 1.
 #include <cuda.h>
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t lim = wait_limit(status);
   const long long ntiles = g.n / kCRows;
   const uint32_t sw1 = smem_u32(smem + kOffW1), sw2 = smem_u32(smem + kOffW2);
   const uint32_t sw3 = smem_u32(smem + kOffW3), sa1 = smem_u32(smem + kOffA1);
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (*abort_flag) break;
         const int s = issued % kStages, use = issued / kStages;
-        if (!mbar_wait(bar(kBarEmpty + s), (use & 1) ^ 1)) {
+        if (!mbar_wait(bar(kBarEmpty + s), (use & 1) ^ 1, lim)) {
           *abort_flag = 1;
           break;
         }
@@ -247,12 +249,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         if (*abort_flag) break;
         const int j = landed, s = j % kStages, gs = j % kGroups;
-        if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1)) {
+        if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1, lim)) {
           *abort_flag = 1;
           break;
         }
         ++landed;
-        if (!mbar_wait(bar(kBarAcc1E + gs), ((j / kGroups) & 1) ^ 1)) {
+        if (!mbar_wait(bar(kBarAcc1E + gs), ((j / kGroups) & 1) ^ 1, lim)) {
           *abort_flag = 1;
           break;
         }
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     int j = eg;  // the block's tile index
     for (long long tile = blockIdx.x + (long long)eg * gridDim.x; tile < ntiles;
          tile += (long long)kGroups * gridDim.x, j += kGroups) {
-      bool ok = mbar_wait(bar(kBarAcc1F + eg), (j / kGroups) & 1);
+      bool ok = mbar_wait(bar(kBarAcc1F + eg), (j / kGroups) & 1, lim);
       if (group_any(eg, !ok || *abort_flag)) {
         *abort_flag = 1;
         break;
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                idesc_bf16(kCRows, kMlpHidden), ks > 0);
         umma_commit(bar(kBarL2 + eg));
       }
-      ok = mbar_wait(bar(kBarL2 + eg), ph2);
+      ok = mbar_wait(bar(kBarL2 + eg), ph2, lim);
       ph2 ^= 1;
       if (group_any(eg, !ok)) {
         *abort_flag = 1;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                ks > 0);
         umma_commit(bar(kBarL3 + eg));
       }
-      ok = mbar_wait(bar(kBarL3 + eg), ph3);
+      ok = mbar_wait(bar(kBarL3 + eg), ph3, lim);
       ph3 ^= 1;
       if (group_any(eg, !ok)) {
         *abort_flag = 1;

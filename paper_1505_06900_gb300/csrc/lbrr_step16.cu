@@ -212,8 +212,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < kRowWaitLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity,
+                                          uint32_t limit = kRowWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     uint32_t ok;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -281,6 +282,9 @@ __global__ void __launch_bounds__(row16_max_nx<Q>() / 2)
       reinterpret_cast<uint64_t *>(smem_row + kRowBufs * buf_elems * sizeof(T));
   const int tid = threadIdx.x;
   const uint32_t row_bytes = (uint32_t)(nx * sizeof(T));
+  // main-loop wait limit: status[1] when positive (host test of the timeout
+  // path), else kRowWaitLimit; the cleanup waits always use kRowWaitLimit
+  const uint32_t lim = status[1] > 0 ? (uint32_t)status[1] : kRowWaitLimit;
 
   if (tid == 0) {
 #pragma unroll
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(row16_max_nx<Q>() / 2)
     int bn = b + kRowDist;
     bn = bn >= kRowBufs ? bn - kRowBufs : bn;
     if (rn < rows) issue_load((int)rn, bn);
-    const bool got = mbar_wait(smem_u32(&mbar[b]), (phases >> b) & 1u);
+    const bool got = mbar_wait(smem_u32(&mbar[b]), (phases >> b) & 1u, lim);
     if (__syncthreads_or(!got)) {
       ok = false;
       break;

@@ -65,10 +65,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t phase) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (uint32_t i = 0; i < kWaitLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase,
+                                          uint32_t limit = kWaitLimit) {
+  for (uint32_t i = 0; i < limit; ++i)
     if (mbar_try_wait(mbar, phase)) return true;
   return false;
+}
+
+// Wait limit of a kernel's main loop: status[1] when positive (set by the
+// host to test the timeout path), else kWaitLimit. Cleanup waits after a
+// timeout always use kWaitLimit, so that copies in flight land.
+__device__ __forceinline__ uint32_t wait_limit(const int *status) {
+  const int v = status[1];
+  return v > 0 ? (uint32_t)v : kWaitLimit;
 }
 
 __device__ __forceinline__ void fence_before() {
