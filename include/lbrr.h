@@ -3,7 +3,7 @@
  * Boltzmann library, liblbrr.so.
  *
  * The method is the regularized collide-and-stream update of Malaspinas,
- * arXiv:1505.06900, Sec. 3.4 (eq_discr_bgk_reg):
+ * arXiv:1505.06900, Sec. 3.5 (eq_discr_bgk_reg):
  *
  *     f_i(x + xi_i, t + 1) = f0_i + (1 - 1/tau) f1_i,
  *
@@ -12,7 +12,7 @@
  * (eq_fone_d2q9 / eq_fone_d3q27) whose coefficients of order n >= 3 follow
  * from u and a1^(2) = Pi^(1) by the recursion of Sec. 3.1 (eq_rel_a1,
  * Appendix B without the starred terms), and tau is the shifted relaxation
- * time tau-bar of Sec. 3.3 (kinematic viscosity nu = (tau - 1/2) / 3).
+ * time tau-bar of Sec. 3.4 (kinematic viscosity nu = (tau - 1/2) / 3).
  *
  * Conventions shared by every call:
  *  - Lattices: D2Q9 (nz must be 1) and D3Q27. Velocity i has components
@@ -60,10 +60,10 @@ extern "C" {
 #define LB_STORE_BF16 2 /* (f_i - w_i) / w_i as bfloat16, round to nearest even */
 
 /* collision models */
-#define LB_COLLIDE_RR 0   /* recursive regularized, Sec. 3.4 (the paper's model) */
-#define LB_COLLIDE_REG2 1 /* order-2 regularized comparator, Sec. 3.6.1 (eq_feq_2) */
+#define LB_COLLIDE_RR 0   /* recursive regularized, Sec. 3.5 (the paper's model) */
+#define LB_COLLIDE_REG2 1 /* order-2 regularized comparator, Sec. 3.8.1 (eq_feq_2) */
 #define LB_COLLIDE_BGK 2  /* plain BGK, f - (f - f0)/tau with the full-basis f0 of Sec. 3.2
-                             (eq_full_discr_bgk, Sec. 3.3); initialised like RR */
+                             (eq_full_discr_bgk, Sec. 3.4); initialised like RR */
 
 /* initialisation modes of lb_init_fields */
 #define LB_INIT_EQ 0        /* f = f0(rho, u) */
@@ -75,7 +75,7 @@ typedef struct lb_ctx lb_ctx;
 typedef struct lb_options {
   int lattice;    /* LB_D2Q9 or LB_D3Q27 */
   int nx, ny, nz; /* grid size in cells, each >= 1; nz == 1 for D2Q9 */
-  double tau;     /* shifted relaxation time tau-bar > 1/2 (Sec. 3.3) */
+  double tau;     /* shifted relaxation time tau-bar > 1/2 (Sec. 3.4) */
   int periodic;   /* must be 1: every face without a wall is periodic */
   int storage;    /* LB_STORE_* */
   int collision;  /* LB_COLLIDE_* */
@@ -83,7 +83,7 @@ typedef struct lb_options {
                      node planes of these axes (each >= 3 nodes), 0 = none */
 } lb_options;
 
-/* No-slip walls (Sec. 3.5, boundary conditions): the boundary nodes lie on
+/* No-slip walls (Sec. 3.7, boundary conditions): the boundary nodes lie on
  * the walls and carry u = 0; each is closed by the regularized Dirichlet
  * procedure in its zero-velocity form (an unknown population, one that would
  * stream in from outside, takes the value of its opposite, so rho and
@@ -105,7 +105,7 @@ typedef struct lb_options {
  * populations start at rest (f = w, rho = 1, u = 0). Storage F32, model RR.
  * Returns LB_EINVAL for a bad lattice, a size < 1, nz != 1 with D2Q9,
  * tau <= 1/2 or periodic != 1; LB_ENOMEM if the store does not fit. No walls.
- * Sec. 3.2 (q populations per node), Sec. 3.3 (tau). */
+ * Sec. 3.2 (q populations per node), Sec. 3.4 (tau). */
 LB_API int lb_create(lb_ctx **out, int lattice, int nx, int ny, int nz, double tau, int periodic);
 
 /* As lb_create, with the storage precision, collision model and walls

@@ -1,4 +1,4 @@
-"""Von Neumann linear stability of the oracle's collide-and-stream update (Sec. 3.5).
+"""Von Neumann linear stability of the oracle's collide-and-stream update (Sec. 3.6).
 
 TEST INFRASTRUCTURE (part of the oracle). The linearised scheme is
 f'_i(x + xi_i, t+1) = sum_j Lambda_ij f'_j(x, t) with Lambda the Jacobian of the

@@ -1,6 +1,6 @@
 // Device-side building blocks of the recursive-regularized (RR) BGK step
 // (arXiv:1505.06900): storage conversion, moments, and the reconstruction
-// f_post = f0 + (1 - 1/tau) f1 of Sec. 3.4 on the D2Q9 / D3Q27 Hermite bases.
+// f_post = f0 + (1 - 1/tau) f1 of Sec. 3.5 on the D2Q9 / D3Q27 Hermite bases.
 //
 // The kernel does not evaluate the paper's Hermite sums term by term. Both
 // lattices are tensor products of the D1Q3 rule, so their Hermite bases are
@@ -203,7 +203,7 @@ __device__ __forceinline__ void synth1(float c0, float c1, float c2, float &om, 
 }
 
 // Coefficients of the shifted post-collision populations of a D2Q9 cell
-// (RR, Sec. 3.4): df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1
+// (RR, Sec. 3.5): df_post = f0 + om1 f1 - w with om1 = 1 - 1/tau (om1 = 1
 // rebuilds f0 + f1). Coefficient of x^a y^b: C = px[a] Q1[b] + h[a] Q2[b] +
 // dx[a] Q3[b] with px = (1, ux, ux^2), h = (0, 0, 1), dx = (0, 1, 2 ux) (powers
 // of ux and their second and first ux-derivatives) and the y-vectors
@@ -229,7 +229,7 @@ __device__ __forceinline__ void coeffs_rr_d2q9(const Macro &m, float om1, float 
   c[0][1] = m.jy;
 }
 
-// Order-2 regularized comparator (Sec. 3.6.1, eq_feq_2): only the
+// Order-2 regularized comparator (Sec. 3.8.1, eq_feq_2): only the
 // coefficients of total Hermite order <= 2 are kept, for f0 and for f1.
 __device__ __forceinline__ void coeffs_reg2_d2q9(const Macro &m, float om1, float (&c)[3][3]) {
 #pragma unroll
@@ -281,7 +281,7 @@ __device__ __forceinline__ void synth_tensor_d3q27(const float (&c)[3][3][3], fl
 }
 
 // Coefficients of the shifted post-collision populations of a D3Q27 cell
-// (RR, Sec. 3.4). The coefficient of x^a y^b z^c is C = px[a] Q1[b][c] +
+// (RR, Sec. 3.5). The coefficient of x^a y^b z^c is C = px[a] Q1[b][c] +
 // h[a] Q2[b][c] + dx[a] Q3[b][c] (px, h, dx as in 2D) with the (y, z) matrices
 //   Q1 = rho py pz + om1 (Pi_yy h_y pz + Pi_zz py h_z + Pi_yz dy dz)
 //   Q2 = om1 Pi_xx py pz,   Q3 = om1 (Pi_xy dy pz + Pi_xz py dz),
@@ -402,7 +402,7 @@ __host__ __device__ constexpr int vel(int i, int a) {
 
 // Grid geometry passed by value to every kernel. walls: bit a set = axis a
 // is bounded by no-slip walls through its first and last node planes
-// (Sec. 3.5, boundary conditions); other axes are periodic.
+// (Sec. 3.7, boundary conditions); other axes are periodic.
 struct Grid {
   int nx, ny, nz;
   long long n;  // nx * ny * nz (cells per population slot)
@@ -455,7 +455,7 @@ __device__ __forceinline__ uint32_t opposite_mask(uint32_t m) {
 }
 
 // Zero-velocity no-slip closure of a boundary node (the regularized
-// Dirichlet procedure of Sec. 3.5 with u_bc = 0), on shifted populations:
+// Dirichlet procedure of Sec. 3.7 with u_bc = 0), on shifted populations:
 // with u_bc = 0 the equilibrium is the same for a population and its
 // opposite, so giving an unknown population the value of its known opposite
 // is the off-equilibrium bounce-back from which the lattice symmetries give

@@ -7,7 +7,7 @@
 // separable moment passes as the integer ratios 1 : 4 : 1 and are divided out
 // of the synthesis T/w = (c0 - 3/2 c2, c0 +- 3 c1 + 3 c2).
 //
-// Coefficient tensor (Sec. 3.4 with eq_rel_a1 in closed form): the
+// Coefficient tensor (Sec. 3.5 with eq_rel_a1 in closed form): the
 // coefficient of x^a y^b z^c of f0 + om1 f1 is rho ux^a uy^b uz^c plus om1
 // times the pair sum of a1^(2) over the index pairs of x^a y^b z^c; it is
 // written out below per (b, c) with the products by 0 and 1 removed, since
@@ -292,7 +292,7 @@ __device__ __forceinline__ void coeffs27_eq(const Macro2 &m, V (&c)[3][3][3]) {
   c[0][0][1] = m.jz;
 }
 
-// Order-2 regularized coefficients (Sec. 3.6.1): total order <= 2 only.
+// Order-2 regularized coefficients (Sec. 3.8.1): total order <= 2 only.
 __device__ __forceinline__ void coeffs_reg2_9(const Macro2 &m, V (&c)[3][3]) {
   const V z = bc(0.0f);
 #pragma unroll

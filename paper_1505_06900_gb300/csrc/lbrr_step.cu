@@ -1,5 +1,5 @@
 // Fused collide-and-stream kernel of the recursive-regularized BGK scheme
-// (arXiv:1505.06900, Sec. 3.4, eq_discr_bgk_reg) on an AA-pattern store.
+// (arXiv:1505.06900, Sec. 3.5, eq_discr_bgk_reg) on an AA-pattern store.
 //
 // AA pattern: one population buffer, updated in place. With the store in
 // natural order (parity 0), population i of cell x sits in slot i of x. An

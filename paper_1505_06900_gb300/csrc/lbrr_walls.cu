@@ -1,4 +1,4 @@
-// Collide-and-stream update with no-slip walls (Sec. 3.5, boundary
+// Collide-and-stream update with no-slip walls (Sec. 3.7, boundary
 // conditions) on an AA-pattern store, for grids whose Grid::walls is set.
 //
 // The walls pass through the first and last node planes of the walled axes:

@@ -1,4 +1,4 @@
-"""No-slip walls (Sec. 3.5, boundary conditions) on the GPU, against the FP64
+"""No-slip walls (Sec. 3.7, boundary conditions) on the GPU, against the FP64
 oracle, and the dipole-wall benchmark (Sec. 4.1) against the enstrophy peaks
 the paper prints.
 
@@ -150,7 +150,7 @@ def test_dipole_enstrophy_peaks_match_the_paper(N, tol):
 def test_dipole_at_mach_0_7_stays_stable_with_rr_only():
     """Sec. 4.1 runs the dipole at a peak Mach number of 0.7 (U_lb = 0.032,
     Re = 2500) with the recursive model; the order-2 regularized model of
-    Sec. 3.6.1, whose shear modes the paper finds unstable at high velocity,
+    Sec. 3.8.1, whose shear modes the paper finds unstable at high velocity,
     blows up on the same run."""
     r = dipole.run(250, t_end=0.75, u_lb=0.032)
     assert all(np.isfinite(p["enstrophy"]) for p in r["peaks"])

@@ -1,4 +1,4 @@
-"""Pins of the oracle's no-slip walls (Sec. 3.5, boundary conditions) and of
+"""Pins of the oracle's no-slip walls (Sec. 3.7, boundary conditions) and of
 the dipole-wall set-up (Sec. 4.1), against closed forms that do not go
 through the oracle's formulas:
 
@@ -16,7 +16,7 @@ import oracle as O
 from paper_1505_06900_gb300 import workloads as W
 
 
-@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q27])
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q27, O.D3Q19])
 def test_channel_wave_decays_at_the_stokes_rate(lattice):
     H, tau = 32, 0.8
     D = 2 if lattice == O.D2Q9 else 3
@@ -39,7 +39,8 @@ def test_channel_wave_decays_at_the_stokes_rate(lattice):
 
 @pytest.mark.parametrize("lattice,shape,walls", [(O.D2Q9, (5, 6, 1), 3),
                                                  (O.D3Q27, (4, 5, 3), 7),
-                                                 (O.D3Q27, (4, 5, 3), 5)])
+                                                 (O.D3Q27, (4, 5, 3), 5),
+                                                 (O.D3Q19, (4, 5, 3), 7)])
 def test_rest_state_is_a_fixed_point_of_the_walls(lattice, shape, walls):
     D = 2 if lattice == O.D2Q9 else 3
     nx, ny, nz = shape
