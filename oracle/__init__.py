@@ -26,9 +26,10 @@ _LIB_PATH = os.path.join(_BUILD, "liblbrr_oracle.so")
 
 D2Q9 = 9
 D3Q27 = 27
-RR = 0        # recursive-regularized model (Sec. 3.4)
-REG2 = 1      # order-2 regularized comparator (Sec. 3.6.1)
-BGK = 2       # plain BGK with the full-basis equilibrium (Sec. 3.3)
+D3Q19 = 19    # D3Q27 without the corners; order-3 basis of sums / differences
+RR = 0        # recursive-regularized model (Sec. 3.5)
+REG2 = 1      # order-2 regularized comparator (Sec. 3.8.1)
+BGK = 2       # plain BGK with the full-basis equilibrium (Sec. 3.4)
 INIT_EQ = 0
 INIT_EQ_NEQ_FD = 1
 
@@ -107,6 +108,8 @@ def dims_of(lattice: int) -> tuple[int, int]:
         return 2, 9
     if lattice == D3Q27:
         return 3, 27
+    if lattice == D3Q19:
+        return 3, 19
     raise ValueError(f"unknown lattice {lattice}")
 
 
@@ -124,13 +127,16 @@ def lattice_tables(lattice: int):
 
 
 def hermite_basis(lattice: int):
-    """Kept Hermite polynomials H [Q,Q] (row k, column i) and prefactors [Q]."""
+    """Kept basis polynomials H [K,Q] (row k, column i) and prefactors [K]:
+    K = Q for D2Q9 / D3Q27; K = 16 for D3Q19 (orders 0..2 and the six
+    order-3 sums / differences H_aab +- H_bcc)."""
     lib = _load()
     _, Q = dims_of(lattice)
     H = np.zeros(Q * Q)
     p = np.zeros(Q)
     _check(lib.ora_hermite_basis(lattice, _dp(H), _dp(p)), "hermite_basis")
-    return H.reshape(Q, Q), p
+    K = 16 if lattice == D3Q19 else Q
+    return H.reshape(Q, Q)[:K], p[:K]
 
 
 def feq_cell(lattice: int, rho: float, u, variant: int = RR) -> np.ndarray:

@@ -14,22 +14,37 @@
  *   a1^(3..6) by the recursion    (Sec. 3.1 eq_rel_a1, written out in Appendix B,
  *                                  with the starred O(Ma^(n+1)) terms dropped)
  *   f1                            (Sec. 3.2, eq_fone_d2q9 / eq_fone_d3q27)
- *   f_post = f0 + (1 - 1/tau) f1  (Sec. 3.4, eq_discr_bgk_reg; tau is the
- *                                  shifted relaxation time tau-bar of Sec. 3.3)
+ *   f_post = f0 + (1 - 1/tau) f1  (Sec. 3.5, eq_discr_bgk_reg; tau is the
+ *                                  shifted relaxation time tau-bar of Sec. 3.4)
  *   streaming f_i(x + xi_i, t+1)  (eq_discr_bgk_reg), periodic wrap, with a
  *                                  plain two-array pull update.
  *
- * No-slip walls (Sec. 3.5, boundary conditions): the regularized Dirichlet
+ * No-slip walls (Sec. 3.7, boundary conditions): the regularized Dirichlet
  * procedure with u_bc = 0 on boundary nodes that lie on the walls (rho from
  * the lattice symmetries, f0(rho, u_bc), Pi^(1) from the symmetries,
  * f1 = w / (2 cs^4) H2 : Pi^(1), all populations replaced by f0 + f1), then
  * the usual collision; see wall_regularize.
  *
- * The order-2 regularized model of Sec. 3.6.1 (eq_feq_2) is the comparator
- * variant ORA_REG2; ORA_BGK is the plain BGK update of Sec. 3.3
+ * The order-2 regularized model of Sec. 3.8.1 (eq_feq_2) is the comparator
+ * variant ORA_REG2; ORA_BGK is the plain BGK update of Sec. 3.4
  * (eq_full_discr_bgk) with the same full-basis equilibrium. Everything is plain loops in double precision; no
  * blocking, fusion or reordering beyond the formulas. Population arrays are
  * laid out f[i][z][y][x] (x fastest), i = (cx+1) + 3(cy+1) + 9(cz+1).
+ *
+ * D3Q19 (the paper leaves its recursion open, Sec. 5): the D3Q27 velocities
+ * without the eight corners, weights 1/3, 1/18, 1/36. That rule integrates
+ * polynomials up to degree five exactly, so orders 0..2 keep their Hermite
+ * norms; order-3 products have degree six and are not exact there:
+ * <H_xxy, H_yzz> = -cs^6 on D3Q19 (0 on D3Q27), xyz vanishes on every D3Q19
+ * velocity, and the order-4 members are not orthogonal to order 2
+ * (<H_xxyy, H_zz> = -cs^6). The basis kept is therefore 1, xi, H2 and, for
+ * each odd index b with even pair (a, c), H_aab + H_bcc and H_aab - H_bcc,
+ * which D3Q19 keeps orthogonal to each other and to the lower orders with
+ * norms 2 cs^6 and 6 cs^6. f0 and f1 are the expansions on that basis
+ * whose coefficients are the projections of the Hermite coefficients
+ * (a_aab +- a_bcc) given by Sec. 2 (f0) and by the recursion (f1); with the
+ * sum and the difference both kept, every order-3 Hermite moment except xyz
+ * is reproduced.
  *
  * Readings of the paper that this file depends on:
  *  - lattice weights and c_s^2 = 1/3: the paper names D2Q9/D3Q27 Gauss-Hermite
@@ -56,6 +71,7 @@
 
 #define ORA_D2Q9 9
 #define ORA_D3Q27 27
+#define ORA_D3Q19 19
 #define ORA_RR 0
 #define ORA_REG2 1
 #define ORA_BGK 2
@@ -79,6 +95,21 @@ static int make_lattice(int lattice, ora_lattice *L) {
   } else if (lattice == ORA_D3Q27) {
     L->d = 3;
     L->q = 27;
+  } else if (lattice == ORA_D3Q19) {
+    /* D3Q27 order without the corners; weights by |xi|^2 = 0, 1, 2 */
+    static const double w19[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    L->d = 3;
+    L->q = 19;
+    int k = 0;
+    for (int i = 0; i < 27; ++i) {
+      const int c[3] = {i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1};
+      const int m = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+      if (m == 3) continue;
+      for (int a = 0; a < 3; ++a) L->c[k][a] = c[a];
+      L->w[k] = w19[m];
+      ++k;
+    }
+    return 0;
   } else {
     return -1;
   }
@@ -106,7 +137,8 @@ typedef struct {
 static double h2(double x) { return x * x - cs2; }
 
 /* Hermite expansion of a population set, Sec. 3.2 (the expansion of f_i for
- * D2Q9 and for D3Q27): f_i = w_i ( c0 + xi.c1/cs2 + H2:a2/(2cs4) + ... ).
+ * D2Q9 and for D3Q27; D3Q19 on the basis described in the header):
+ * f_i = w_i ( c0 + xi.c1/cs2 + H2:a2/(2cs4) + ... ).
  * c0 is the order-0 coefficient, c1 the order-1 coefficient, a the orders 2..6.
  */
 static double hermite_sum(const ora_lattice *L, int i, double c0, const double c1[3],
@@ -120,6 +152,18 @@ static double hermite_sum(const ora_lattice *L, int i, double c0, const double c
     s += (h2(x) * a->xx + 2.0 * x * y * a->xy + h2(y) * a->yy) / (2.0 * cs4);
     s += (h2(x) * y * a->xxy + x * h2(y) * a->xyy) / (2.0 * cs6);
     s += h2(x) * h2(y) * a->xxyy / (4.0 * cs8);
+  } else if (L->q == 19) {
+    s += (x * c1[0] + y * c1[1] + z * c1[2]) / cs2;
+    s += (h2(x) * a->xx + h2(y) * a->yy + h2(z) * a->zz +
+          2.0 * (x * y * a->xy + x * z * a->xz + y * z * a->yz)) /
+         (2.0 * cs4);
+    /* order 3 on D3Q19: H_aab + H_bcc (norm 2 cs^6), H_aab - H_bcc (6 cs^6) */
+    s += (x * (h2(y) + h2(z)) * (a->xyy + a->xzz) + y * (h2(x) + h2(z)) * (a->xxy + a->yzz) +
+          z * (h2(x) + h2(y)) * (a->xxz + a->yyz)) /
+         (2.0 * cs6);
+    s += (x * (y * y - z * z) * (a->xyy - a->xzz) + y * (x * x - z * z) * (a->xxy - a->yzz) +
+          z * (x * x - y * y) * (a->xxz - a->yyz)) /
+         (6.0 * cs6);
   } else {
     s += (x * c1[0] + y * c1[1] + z * c1[2]) / cs2;
     s += (h2(x) * a->xx + h2(y) * a->yy + h2(z) * a->zz +
@@ -226,7 +270,7 @@ static void recursive_coefficients(int d, const double u[3], hcoef *a) {
 }
 
 /* f1_i of eq_fone_d2q9 / eq_fone_d3q27 from the coefficients a1. With variant
- * ORA_REG2 only the order-two term is kept (Sec. 3.6.1). */
+ * ORA_REG2 only the order-two term is kept (Sec. 3.8.1). */
 static double fneq(const ora_lattice *L, int variant, int i, const hcoef *a1) {
   const double zero[3] = {0.0, 0.0, 0.0};
   if (variant == ORA_BGK) variant = ORA_RR;
@@ -312,7 +356,11 @@ int ora_lattice_tables(int lattice, int *d, int *q, int *c /* q*3 */, double *w 
  * prefactor of each in the expansion of f (Sec. 3.2). Rows follow the order
  * 1, x, y, (z), xx, xy, (xz), yy, (yz), (zz), then order 3..6 as in hcoef.
  * mult[k] is the number of index orderings of member k, so that the expansion
- * term is w_i * pref[k] * H_k,i * a_k with pref = mult/(n! cs^(2n)). */
+ * term is w_i * pref[k] * H_k,i * a_k with pref = mult/(n! cs^(2n)).
+ * D3Q19: 16 rows, 1, x, y, z, the six of order 2, then H_xyy + H_xzz,
+ * H_xxy + H_yzz, H_xxz + H_yyz (pref 1/(2 cs^6)) and the three differences
+ * (pref 1/(6 cs^6)), a_k being the sum or difference of the two Hermite
+ * coefficients; the remaining rows are left untouched. */
 int ora_hermite_basis(int lattice, double *H /* q*q */, double *pref /* q */) {
   ora_lattice L;
   if (make_lattice(lattice, &L)) return -1;
@@ -330,7 +378,21 @@ int ora_hermite_basis(int lattice, double *H /* q*q */, double *pref /* q */) {
     ROW(1.0, 1.0);
     ROW(x, 1.0 / cs2);
     ROW(y, 1.0 / cs2);
-    if (L.d == 2) {
+    if (L.q == 19) {
+      ROW(z, 1.0 / cs2);
+      ROW(h2(x), 1.0 / (2.0 * cs4));
+      ROW(x * y, 2.0 / (2.0 * cs4));
+      ROW(x * z, 2.0 / (2.0 * cs4));
+      ROW(h2(y), 1.0 / (2.0 * cs4));
+      ROW(y * z, 2.0 / (2.0 * cs4));
+      ROW(h2(z), 1.0 / (2.0 * cs4));
+      ROW(x * (h2(y) + h2(z)), 1.0 / (2.0 * cs6));
+      ROW(y * (h2(x) + h2(z)), 1.0 / (2.0 * cs6));
+      ROW(z * (h2(x) + h2(y)), 1.0 / (2.0 * cs6));
+      ROW(x * (y * y - z * z), 1.0 / (6.0 * cs6));
+      ROW(y * (x * x - z * z), 1.0 / (6.0 * cs6));
+      ROW(z * (x * x - y * y), 1.0 / (6.0 * cs6));
+    } else if (L.d == 2) {
       ROW(h2(x), 1.0 / (2.0 * cs4));
       ROW(x * y, 2.0 / (2.0 * cs4));
       ROW(h2(y), 1.0 / (2.0 * cs4));
@@ -633,7 +695,7 @@ int ora_enstrophy(int lattice, int nx, int ny, int nz, const double *f, double *
 }
 
 /* ------------------------------------------------------------------------ */
-/* No-slip walls (Sec. 3.5, the boundary-conditions paragraph)               */
+/* No-slip walls (Sec. 3.7, the boundary-conditions subsection)               */
 /*                                                                          */
 /* walls: bit a set = axis a is bounded by no-slip walls that pass through   */
 /* its first and last node planes (the boundary nodes lie on the walls and   */

@@ -19,6 +19,9 @@ from paper_1505_06900_gb300 import workloads as W
 CS2 = 1.0 / 3.0
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 LATTICES = [O.D2Q9, O.D3Q27]
+# pins that hold for any of the three lattices (D3Q19 keeps an incomplete,
+# non-tensor basis: its own pins are in test_oracle_d3q19.py)
+ALL_LATTICES = [O.D2Q9, O.D3Q27, O.D3Q19]
 
 
 def rand_u(rng, d, scale=0.15):
@@ -146,12 +149,13 @@ def test_equilibrium_closed_product_form(lat):
         assert np.allclose(f0, ref, rtol=0, atol=1e-15)
 
 
-def test_order2_equilibrium_textbook():
+@pytest.mark.parametrize("lat", [O.D3Q27, O.D3Q19])
+def test_order2_equilibrium_textbook(lat):
     """eq_feq_2: the order-2 equilibrium is the textbook
     w rho (1 + 3 xi.u + 9/2 (xi.u)^2 - 3/2 u^2)."""
-    c, w = O.lattice_tables(O.D3Q27)
+    c, w = O.lattice_tables(lat)
     u = np.array([0.1, -0.07, 0.05])
-    f = O.feq_cell(O.D3Q27, 1.1, u, variant=O.REG2)
+    f = O.feq_cell(lat, 1.1, u, variant=O.REG2)
     cu = c @ u
     ref = w * 1.1 * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * u @ u)
     assert np.allclose(f, ref, atol=1e-15)
@@ -179,7 +183,7 @@ NAMES_3D = ["xx", "xy", "xz", "yy", "yz", "zz", "xxy", "xxz", "xyy", "xzz", "yzz
             "xxyy", "xxzz", "yyzz", "xyzz", "xyyz", "xxyz", "xxyzz", "xxyyz", "xyyzz", "xxyyzz"]
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_recursion_equals_pair_sum_closed_form(lat):
     """eq_rel_a1 (Appendix B without the starred terms): a1^(n) equals the sum,
     over unordered pairs of index positions, of a1^(2) on that pair times the
@@ -197,7 +201,7 @@ def test_recursion_equals_pair_sum_closed_form(lat):
             assert abs(val - _pair_sum(d, idx, u, A)) < 1e-15, name
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_fneq_is_second_velocity_derivative_of_feq(lat):
     """With a1^(n) given by the recursion, f1 = 1/2 sum_ab a1^(2)_ab
     d^2 (f0/rho) / du_a du_b. f0/rho is a polynomial of degree <= 2 in each
@@ -224,9 +228,9 @@ def test_fneq_is_second_velocity_derivative_of_feq(lat):
         assert np.allclose(O.fneq_cell(lat, u, p), ref, rtol=0, atol=1e-14)
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_fneq_at_rest_is_order_two(lat):
-    """Sec. 3.5 (boundary conditions): at u = 0 the off-equilibrium part reduces
+    """Sec. 3.7 (boundary conditions): at u = 0 the off-equilibrium part reduces
     to f1 = w/(2 cs4) H2 : Pi1 exactly."""
     c, w = O.lattice_tables(lat)
     d, _ = O.dims_of(lat)
@@ -241,7 +245,7 @@ def test_fneq_at_rest_is_order_two(lat):
 
 # -------------------------------------------------------------- collision ----
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 @pytest.mark.parametrize("variant", [O.RR, O.REG2, O.BGK])
 def test_collision_moments(lat, variant):
     """eq_discr_bgk_reg: post-collision populations keep rho and rho u and
@@ -269,7 +273,7 @@ def test_collision_moments(lat, variant):
         assert np.allclose(p2, Pi[iu], atol=1e-15)
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_bgk_relaxes_every_hermite_coefficient(lat):
     """eq_full_discr_bgk: plain BGK scales every Hermite coefficient of
     f - f0 by (1 - 1/tau), the ones of order > 2 included (which RR replaces by
@@ -288,7 +292,7 @@ def test_bgk_relaxes_every_hermite_coefficient(lat):
         assert np.abs(H[1 + d + d * (d + 1) // 2:] @ (rr - post)).max() > 1e-6
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_collision_fixed_points(lat):
     """f = f0 is a fixed point; tau = 1 gives f_post = f0 for any f."""
     c, w = O.lattice_tables(lat)
@@ -302,7 +306,7 @@ def test_collision_fixed_points(lat):
     assert np.allclose(O.collide_cell(lat, f, 1.0), O.feq_cell(lat, rho, uu), atol=1e-16)
 
 
-@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("lat", ALL_LATTICES)
 def test_regularization_is_a_projection(lat):
     """eq_reg: regularizing twice equals regularizing once (tau -> infinity is
     f_post = f0 + f1), and the regularized f keeps rho, rho u and Pi1."""
@@ -338,7 +342,8 @@ def _brute_step(lat, shape, tau, f):
     return out
 
 
-@pytest.mark.parametrize("lat,shape", [(O.D2Q9, (5, 4, 1)), (O.D3Q27, (4, 5, 3))])
+@pytest.mark.parametrize("lat,shape", [(O.D2Q9, (5, 4, 1)), (O.D3Q27, (4, 5, 3)),
+                                       (O.D3Q19, (3, 4, 5))])
 def test_step_matches_collide_then_roll(lat, shape):
     """eq_discr_bgk_reg with periodic wrap: f_i(x + xi_i, t+1) = f_post_i(x, t),
     checked by brute force on a tiny non-cubic grid."""
@@ -351,7 +356,8 @@ def test_step_matches_collide_then_roll(lat, shape):
     assert np.allclose(got, ref, rtol=0, atol=1e-16)
 
 
-@pytest.mark.parametrize("lat,shape", [(O.D2Q9, (8, 6, 1)), (O.D3Q27, (6, 5, 4))])
+@pytest.mark.parametrize("lat,shape", [(O.D2Q9, (8, 6, 1)), (O.D3Q27, (6, 5, 4)),
+                                       (O.D3Q19, (5, 4, 6))])
 def test_conservation_and_uniform_flow(lat, shape):
     """Mass and momentum are conserved to round-off on a periodic grid
     (Sec. 2 conservation), and a uniform flow stays uniform at f0."""
@@ -371,18 +377,19 @@ def test_conservation_and_uniform_flow(lat, shape):
     assert np.allclose(f2, f0[:, None, None, None], atol=1e-15)
 
 
-def test_single_population_moves_one_cell_per_step():
+@pytest.mark.parametrize("lat", [O.D3Q27, O.D3Q19])
+def test_single_population_moves_one_cell_per_step(lat):
     """Streaming: with tau = 1 the post-collision state is f0 of the cell, so a
     one-cell density bump at rest spreads as w_i * bump to exactly the cells
     x + xi_i after one step (brute force on 3^3)."""
     shape = (3, 3, 3)
-    c, w = O.lattice_tables(O.D3Q27)
+    c, w = O.lattice_tables(lat)
     rho = np.ones((3, 3, 3))
     rho[1, 1, 1] = 1.5
     u = np.zeros((3, 3, 3, 3))
-    f = O.init(O.D3Q27, shape, 1.0, rho, u, O.INIT_EQ)
-    f1 = O.step(O.D3Q27, shape, 1.0, f, 1)
-    for i in range(27):
+    f = O.init(lat, shape, 1.0, rho, u, O.INIT_EQ)
+    f1 = O.step(lat, shape, 1.0, f, 1)
+    for i in range(len(w)):
         expect = np.full((3, 3, 3), w[i])
         expect[1 + c[i, 2], 1 + c[i, 1], 1 + c[i, 0]] = 1.5 * w[i]
         assert np.allclose(f1[i], expect, atol=1e-16)
@@ -457,7 +464,7 @@ def test_enstrophy_3d_closed_form():
 def test_taylor_green_2d_decay():
     """Config D2Q9 128^2 Taylor-Green vortex, Re = 100, 1000 steps: the kinetic
     energy decays as exp(-4 nu k^2 t) with nu = cs2 (tau - 1/2) (Sec. 3.3 with
-    the shifted tau), fitted nu within 1%; the velocity field stays within 1%
+    the shifted tau of Sec. 3.4), fitted nu within 1%; the velocity field stays within 1%
     (L2) of the analytic field. The L2 tolerance covers the O(Ma^2) acoustic
     content of the weakly compressible scheme (measured 5.9e-3)."""
     n, U = 128, 0.05
@@ -487,7 +494,7 @@ def _golden_stability():
 
 
 def test_linear_stability_present_model_stable_at_ma_0346():
-    """Sec. 3.5: at tau = 0.5001, u = (0.2, 0) the present model has no unstable
+    """Sec. 3.6: at tau = 0.5001, u = (0.2, 0) the present model has no unstable
     mode anywhere in the k plane (growth rate ln|lambda| <= 0 up to the
     round-off of the numerical Jacobian)."""
     g = _golden_stability()
@@ -496,14 +503,14 @@ def test_linear_stability_present_model_stable_at_ma_0346():
 
 
 def test_linear_stability_present_model_unstable_at_ma_043():
-    """Sec. 3.5: at u_x = 0.248 unstable modes have appeared."""
+    """Sec. 3.6: at u_x = 0.248 unstable modes have appeared."""
     g = _golden_stability()
     rate, _ = stability.max_growth(O.D2Q9, g["rr_unstable_velocity"], g["tau"], O.RR, nk=64)
     assert rate > 1e-6
 
 
 def test_linear_stability_order2_regularized_unstable_along_kx():
-    """Sec. 3.6.1: the order-2 regularized model has an unstable (shear) mode
+    """Sec. 3.8.1: the order-2 regularized model has an unstable (shear) mode
     along k_y = 0 at u_x = 0.2, while the present model has none there."""
     g = _golden_stability()
     u = g["reg2_unstable_velocity_ky0"]
@@ -515,7 +522,7 @@ def test_linear_stability_order2_regularized_unstable_along_kx():
 
 def test_linear_stability_hydrodynamic_limit():
     """At small k the shear mode of the linearised scheme decays at the
-    Navier-Stokes rate Im(omega_s) = -nu |k|^2 (Sec. 3.5), nu = cs2 (tau - 1/2)."""
+    Navier-Stokes rate Im(omega_s) = -nu |k|^2 (Sec. 3.6), nu = cs2 (tau - 1/2)."""
     tau = 0.8
     nu = CS2 * (tau - 0.5)
     J = stability.jacobian(O.D2Q9, 1.0, (0.0, 0.0), tau)
