@@ -41,11 +41,11 @@ MACH, RE = 0.1, 1600.0
 # + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
 # taken on; reported as null when the sources have changed since.
 # The 512^3 launch is too large for a multi-pass capture; the value is the
-# 256^3 capture (profiles/rr_step_d3q27_f32_f16_256.md, mean of the even and
+# 256^3 capture (profiles/rr_step_d3q19_d3q27_256.md, mean of the even and
 # odd launches, 212.5 B per cell) scaled by the cell count, since the traffic
 # per cell does not depend on the grid size for this streaming kernel.
 TRAFFIC = {
-    "d3q27_f32_512": {"kernel_sha": "17b8f6910189c683", "bytes_per_launch": 28514976768,
+    "d3q27_f32_512": {"kernel_sha": "f93afdb57dff9bb0", "bytes_per_launch": 28514870272,
                       "source": "ncu 256^3 capture scaled to 512^3"},
 }
 
@@ -188,10 +188,11 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm --
 def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_every, stream,
-                 sync_all, sampler=None, keep_u=False, closure=None):
+                 sync_all, sampler=None, keep_u=False, closure=None, lattice=None):
     """Warm up, then time `steps` updates; returns timing and per-launch data
-    (and the final velocity field with keep_u)."""
-    s = B.Solver(B.D3Q27, (n, n, n), tau, storage=storage, stream=stream)
+    (and the final velocity field with keep_u). Lattice D3Q27 unless given."""
+    lattice = B.D3Q27 if lattice is None else lattice
+    s = B.Solver(lattice, (n, n, n), tau, storage=storage, stream=stream)
     try:
         s.init_fields(rho_d, u_d)
         if closure is not None:
@@ -298,6 +299,14 @@ def dipole_variant(B, N: int = 500):
     return out
 
 
+def _peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -352,6 +361,21 @@ def run_gpu(args):
             "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
             "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, same init",
         }
+    # D3Q19 (Sec. 5): 19 populations per cell, the same flow and tau
+    for name, st in (("d3q19_f32", B.STORE_F32), ("d3q19_f16", B.STORE_F16)):
+        r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                         DIAG_EVERY, stream, sync_all, keep_u=True, lattice=B.D3Q19)
+        kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
+        variants[name] = {
+            "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+            "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
+            "roofline_frac": kgbs / (float(_peaks().get("hbm_gbs", 6800.0))),
+            "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
+            "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
+            "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after "
+                           f"{args.warmup + args.steps} steps, same init (lattice + storage "
+                           f"difference)",
+        }
     del u_f32
     variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
                                           sync_all, main["total_ms"] / args.steps)
@@ -383,12 +407,7 @@ def run_gpu(args):
     if rank != 0:
         return 0
 
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peaks = json.load(fh)
-    except OSError:
-        pass
+    peaks = _peaks()
     if "hbm_gbs" in peaks:
         peak, peak_src = float(peaks["hbm_gbs"]), "measured"
     else:

@@ -17,6 +17,16 @@
  * Conventions shared by every call:
  *  - Lattices: D2Q9 (nz must be 1) and D3Q27. Velocity i has components
  *    (i % 3 - 1, (i / 3) % 3 - 1, i / 9 - 1); the opposite velocity is Q-1-i.
+ *    D3Q19, which Sec. 5 names as the cheaper 3-D lattice without defining
+ *    its recursion, is the D3Q27 list with the eight corners (|xi|^2 = 3)
+ *    left out, in the same order (opposite 18-i again), weights 1/3, 1/18,
+ *    1/36. Its quadrature is exact only to total degree five, so its order-3
+ *    basis is, for each odd index b with even pair (a, c), H_aab + H_bcc and
+ *    H_aab - H_bcc (the largest set of order-3 Hermite sums D3Q19 keeps
+ *    orthogonal); f0 and f1 are expanded on 1, xi, H2 and those six, with
+ *    the Hermite coefficients of Sec. 2 (f0) and of the recursion eq_rel_a1
+ *    (f1). Every call accepts it where it accepts D3Q27, except the learned
+ *    closure.
  *  - Fields are structure-of-arrays, x fastest: element (c, z, y, x) of a
  *    field with C components is at ((c * nz + z) * ny + y) * nx + x.
  *  - Populations exchanged with the caller are "shifted": df_i = f_i - w_i,
@@ -52,6 +62,7 @@ extern "C" {
 
 /* lattices */
 #define LB_D2Q9 9
+#define LB_D3Q19 19 /* D3Q27 without the corners; order-3 sums/differences basis */
 #define LB_D3Q27 27
 
 /* storage of the populations in device memory */
@@ -73,7 +84,7 @@ extern "C" {
 typedef struct lb_ctx lb_ctx;
 
 typedef struct lb_options {
-  int lattice;    /* LB_D2Q9 or LB_D3Q27 */
+  int lattice;    /* LB_D2Q9, LB_D3Q19 or LB_D3Q27 */
   int nx, ny, nz; /* grid size in cells, each >= 1; nz == 1 for D2Q9 */
   double tau;     /* shifted relaxation time tau-bar > 1/2 (Sec. 3.4) */
   int periodic;   /* must be 1: every face without a wall is periodic */

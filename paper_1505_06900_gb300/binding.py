@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "liblbrr.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED, LB_ETIMEOUT = 0, 1, 2, 3, 4, 5
-D2Q9, D3Q27 = 9, 27
+D2Q9, D3Q19, D3Q27 = 9, 19, 27
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 COLLIDE_RR, COLLIDE_REG2, COLLIDE_BGK = 0, 1, 2
 WALL_X, WALL_Y, WALL_Z = 1, 2, 4
@@ -100,7 +100,9 @@ def load(path: str | None = None):
 
 
 def dims_of(lattice: int) -> tuple[int, int]:
-    return (2, 9) if lattice == D2Q9 else (3, 27)
+    if lattice not in (D2Q9, D3Q19, D3Q27):
+        raise ValueError(f"unknown lattice {lattice}")
+    return (2, 9) if lattice == D2Q9 else (3, lattice)
 
 
 def _ptr(t) -> int:

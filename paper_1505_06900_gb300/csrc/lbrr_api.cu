@@ -164,7 +164,8 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
   if (!out || !opt) return fail(nullptr, LB_EINVAL, "null argument");
   *out = nullptr;
   const int lat = opt->lattice;
-  if (lat != LB_D2Q9 && lat != LB_D3Q27) return fail(nullptr, LB_EINVAL, "unknown lattice %d", lat);
+  if (lat != LB_D2Q9 && lat != LB_D3Q19 && lat != LB_D3Q27)
+    return fail(nullptr, LB_EINVAL, "unknown lattice %d", lat);
   if (opt->nx < 1 || opt->ny < 1 || opt->nz < 1)
     return fail(nullptr, LB_EINVAL, "grid sizes must be >= 1 (got %d x %d x %d)", opt->nx, opt->ny,
                 opt->nz);

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kAuxThreads)
   float df[Q];
   L::template synth<MODEL>(m, 1.0f, df);
 #pragma unroll
-  for (int i = 0; i < Q; ++i) Storage<S>::template store<D>(f + i * n + cell, i, df[i]);
+  for (int i = 0; i < Q; ++i) Storage<S>::template store<Q>(f + i * n + cell, i, df[i]);
 }
 
 // ----------------------------------------------------------- populations --
@@ -90,12 +90,11 @@ template <int Q, int S>
 __global__ void __launch_bounds__(kAuxThreads)
     set_populations_kernel(typename Storage<S>::T *__restrict__ f, const Grid g,
                            const float *__restrict__ src) {
-  constexpr int D = Lattice<Q>::D;
   const long long cell = (long long)blockIdx.x * kAuxThreads + threadIdx.x;
   if (cell >= g.n) return;
 #pragma unroll
   for (int i = 0; i < Q; ++i)
-    Storage<S>::template store<D>(f + i * g.n + cell, i, src[i * g.n + cell]);
+    Storage<S>::template store<Q>(f + i * g.n + cell, i, src[i * g.n + cell]);
 }
 
 // --------------------------------------------------------------- moments --
@@ -194,8 +193,8 @@ __global__ void __launch_bounds__(kRedThreads)
       const int sl = threadIdx.x;
       int y = r % g.ny, z = r / g.ny;
       if (PARITY) {
-        y = wrap_add(y, vel(sl, 1), g.ny);
-        z = D == 3 ? wrap_add(z, vel(sl, 2), g.nz) : 0;
+        y = wrap_add(y, vel_q<Q>(sl, 1), g.ny);
+        z = D == 3 ? wrap_add(z, vel_q<Q>(sl, 2), g.nz) : 0;
       }
       srow[sl] = (long long)sl * g.n + ((long long)z * g.ny + y) * g.nx;
     }
@@ -206,9 +205,9 @@ __global__ void __launch_bounds__(kRedThreads)
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         const int sl = PARITY ? Q - 1 - i : i;
-        const int cx = PARITY ? vel(sl, 0) : 0;
+        const int cx = PARITY ? vel_q<Q>(sl, 0) : 0;
         const int xs = cx < 0 ? xm : (cx > 0 ? xp : x);
-        df[i] = Storage<S>::template load<D>(f + srow[sl] + xs, i);
+        df[i] = Storage<S>::template load<Q>(f + srow[sl] + xs, i);
       }
       const uint32_t unknown = g.walls ? unknown_mask<Q>(g, x, r % g.ny, r / g.ny) : 0u;
       if (unknown) wall_fill<Q>(unknown, df);
@@ -317,6 +316,10 @@ static void dispatch_qs(int q, int storage, F &&fn) {
     if (storage == 0) fn(integral_constant<int, 9>{}, integral_constant<int, 0>{});
     else if (storage == 1) fn(integral_constant<int, 9>{}, integral_constant<int, 1>{});
     else fn(integral_constant<int, 9>{}, integral_constant<int, 2>{});
+  } else if (q == 19) {
+    if (storage == 0) fn(integral_constant<int, 19>{}, integral_constant<int, 0>{});
+    else if (storage == 1) fn(integral_constant<int, 19>{}, integral_constant<int, 1>{});
+    else fn(integral_constant<int, 19>{}, integral_constant<int, 2>{});
   } else {
     if (storage == 0) fn(integral_constant<int, 27>{}, integral_constant<int, 0>{});
     else if (storage == 1) fn(integral_constant<int, 27>{}, integral_constant<int, 1>{});

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kAux)
   }
 #pragma unroll
   for (int i = 0; i < 27; ++i)
-    Storage<SC>::template store<3>(fc + i * gc.n + cell, i, 0.125f * acc[i]);
+    Storage<SC>::template store<27>(fc + i * gc.n + cell, i, 0.125f * acc[i]);
 }
 
 // ---------------------------------------------------------- closure step --

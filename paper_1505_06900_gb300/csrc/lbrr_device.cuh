@@ -21,6 +21,15 @@
 // float32 round-off relative to the deviations rather than to w, and the
 // conserved coefficients (rho - 1 and rho u) are the moments themselves, so
 // that round-off does not make mass or momentum drift from step to step.
+//
+// D3Q19 (named in Sec. 5 as the cheaper 3-D quadrature whose recursion the
+// paper leaves open) is not a tensor product. It is read as the D3Q27
+// velocities without the eight corners, weights 1/3, 1/18, 1/36. Its
+// quadrature is exact only to total degree five, so at order three it keeps,
+// for each odd index b with even pair (a, c), the sum and the difference
+// H_aab +- H_bcc, which it holds orthogonal to each other and to orders 0-2;
+// the populations are synthesised from those coefficients directly
+// (Lattice<19> below).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -37,6 +46,25 @@ __host__ __device__ constexpr float w1(int k) { return k == 1 ? 2.0f / 3.0f : 1.
 // T(0, 0, 1) at xi = k - 1: the second u-derivative factor (1/2, -1, 1/2)
 __host__ __device__ constexpr float hh1(int k) { return k == 1 ? -1.0f : 0.5f; }
 
+// velocity component a of direction i of D2Q9 / D3Q27
+__host__ __device__ constexpr int vel(int i, int a) {
+  return a == 0 ? i % 3 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1);
+}
+
+// D3Q27 index of D3Q19 direction k: the D3Q27 order with the corners left
+// out (five directions in each of the planes z = -1 and z = +1, nine in
+// z = 0), so that the opposite of k is again 18 - k.
+__host__ __device__ constexpr int q19_to_q27(int k) {
+  return k < 5 ? k + 1 + (k >= 1) + (k >= 4)
+               : (k < 14 ? k + 4 : 19 + (k - 14) + (k >= 15) + (k >= 18));
+}
+
+// velocity component a of direction i of the Q-velocity lattice
+template <int Q>
+__host__ __device__ constexpr int vel_q(int i, int a) {
+  return vel(Q == 19 ? q19_to_q27(i) : i, a);
+}
+
 // weight of velocity i of a D-dimensional tensor-product lattice
 template <int D>
 __host__ __device__ constexpr float weight(int i) {
@@ -49,20 +77,38 @@ __host__ __device__ constexpr float inv_weight(int i) {
                 : (1.0f / w1(i % 3)) * (1.0f / w1((i / 3) % 3)) * (1.0f / w1(i / 9));
 }
 
+// weight of velocity i of the Q-velocity lattice and its inverse (D3Q19:
+// 1/3 at rest, 1/18 on the faces, 1/36 on the edges; inverses exact)
+template <int Q>
+__host__ __device__ constexpr float weight_q(int i) {
+  if (Q != 19) return weight<Q == 9 ? 2 : 3>(i);
+  const int j = q19_to_q27(i);
+  const int m = (vel(j, 0) != 0) + (vel(j, 1) != 0) + (vel(j, 2) != 0);
+  return m == 0 ? 1.0f / 3.0f : (m == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+template <int Q>
+__host__ __device__ constexpr float inv_weight_q(int i) {
+  if (Q != 19) return inv_weight<Q == 9 ? 2 : 3>(i);
+  const int j = q19_to_q27(i);
+  const int m = (vel(j, 0) != 0) + (vel(j, 1) != 0) + (vel(j, 2) != 0);
+  return m == 0 ? 3.0f : (m == 1 ? 18.0f : 36.0f);
+}
+
 // ---------------------------------------------------------------- storage --
 // LB_STORE_F32: df_i as float. LB_STORE_F16 / LB_STORE_BF16: df_i / w_i in
-// 16 bits, round to nearest even.
+// 16 bits, round to nearest even. load<Q> / store<Q> take the direction i of
+// the Q-velocity lattice.
 template <int S>
 struct Storage;
 
 template <>
 struct Storage<0> {
   using T = float;
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static float load(const T *p, int i) {
     return *p;
   }
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static void store(T *p, int i, float v) {
     *p = v;
   }
@@ -71,26 +117,26 @@ struct Storage<0> {
 template <>
 struct Storage<1> {
   using T = __half;
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static float load(const T *p, int i) {
-    return __half2float(*p) * weight<D>(i);
+    return __half2float(*p) * weight_q<Q>(i);
   }
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static void store(T *p, int i, float v) {
-    *p = __float2half_rn(v * inv_weight<D>(i));
+    *p = __float2half_rn(v * inv_weight_q<Q>(i));
   }
 };
 
 template <>
 struct Storage<2> {
   using T = __nv_bfloat16;
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static float load(const T *p, int i) {
-    return __bfloat162float(*p) * weight<D>(i);
+    return __bfloat162float(*p) * weight_q<Q>(i);
   }
-  template <int D>
+  template <int Q>
   __device__ __forceinline__ static void store(T *p, int i, float v) {
-    *p = __float2bfloat16_rn(v * inv_weight<D>(i));
+    *p = __float2bfloat16_rn(v * inv_weight_q<Q>(i));
   }
 };
 
@@ -395,10 +441,133 @@ struct Lattice<27> {
   }
 };
 
-// velocity component a of direction i
-__host__ __device__ constexpr int vel(int i, int a) {
-  return a == 0 ? i % 3 - 1 : (a == 1 ? (i / 3) % 3 - 1 : i / 9 - 1);
+// ----------------------------------------------------------------- D3Q19 --
+// Moments of a D3Q19 cell (direction order of q19_to_q27): the z = 0 plane is
+// a full 3x3 set and takes the separable 2-D sums; the planes z = -1 and
+// z = +1 hold the five-velocity crosses (0,-1), (-1,0), (0,0), (1,0), (0,1);
+// the three plane sums are then combined along z.
+__device__ __forceinline__ Macro moments_d3q19(const float (&f)[19]) {
+  // cross of plane z = -1 (f[0..4]) and z = +1 (f[14..18])
+  const float mxx = f[1] + f[3], myy = f[0] + f[4];
+  const float m0 = (mxx + myy) + f[2], mx = f[3] - f[1], my = f[4] - f[0];
+  const float pxx = f[15] + f[17], pyy = f[14] + f[18];
+  const float p0 = (pxx + pyy) + f[16], px = f[17] - f[15], py = f[18] - f[14];
+  // plane z = 0 (f[5..13], 5 + ix + 3 iy)
+  float s0[3], s1[3], s2[3];
+#pragma unroll
+  for (int l = 0; l < 3; ++l)
+    mom3<false>(f[5 + 3 * l], f[6 + 3 * l], f[7 + 3 * l], s0[l], s1[l], s2[l]);
+  float c00, c01, c02, c10, c11, c20, t0, t1, t2;
+  mom3<false>(s0[0], s0[1], s0[2], c00, c01, c02);
+  mom3<false>(s1[0], s1[1], s1[2], c10, c11, t0);
+  mom3<false>(s2[0], s2[1], s2[2], c20, t1, t2);
+  return macro_from_moments(c00 + (m0 + p0), c10 + (mx + px), c01 + (my + py), p0 - m0,
+                            c20 + (mxx + pxx), c02 + (myy + pyy), p0 + m0, c11, px - mx,
+                            py - my);
 }
+
+// Shifted post-collision populations df = f0 + om1 f1 - w of a D3Q19 cell on
+// the kept basis. A_ab = rho u_a u_b + om1 Pi_ab is the order-2 coefficient;
+// the order-3 Hermite coefficients are A_abb = rho u_a u_b^2 + om1 (Pi_bb u_a
+// + 2 Pi_ab u_b) (f0's rho u u u plus om1 times the recursion eq_rel_a1),
+// i.e. u_a A_bb + 2 u_b om1 Pi_ab. On the kept order-3 members (sum and
+// difference of H_aab and H_bcc) the expansion of f/w reduces, per class of
+// velocity, to
+//   rest:                    drho - 3/2 tr A
+//   face  xi_a = s:          ... + 9/2 A_aa + s (3 j_a - 9 (A_abb + A_acc))
+//   edge  xi_a = s, xi_b = t: ... + 9/2 (A_aa + A_bb) + 9 s t A_ab
+//                                 + s (3 j_a + 9 A_abb) + t (3 j_b + 9 A_aab)
+// with "..." the rest value. The weights 1/3, 1/18, 1/36 are not float32
+// numbers, and multiplying by their roundings would scale mass and momentum
+// by 1 + O(1e-8) at every update, a drift that adds up over thousands of
+// updates. So the edges are formed from the expression above, and the
+// conserved moments close the rest: the odd part of the face pair of axis a
+// is j_a minus the a-momentum of the edges (in exact arithmetic this is
+// w_face 2 (3 j_a - 9 (A_abb + A_acc))), and the rest population is
+// rho - 1 minus the other eighteen. ORDER3 = false drops the order-3
+// members (the order-2 regularized comparator). om1 = 0 gives f0 - w.
+template <bool ORDER3>
+__device__ __forceinline__ void synth_d3q19(const Macro &m, float om1, float (&f)[19]) {
+  const float ux = m.ux, uy = m.uy, uz = m.uz;
+  const float qxy = om1 * m.pxy, qxz = om1 * m.pxz, qyz = om1 * m.pyz;
+  const float axx = fmaf(om1, m.pxx, m.jx * ux), ayy = fmaf(om1, m.pyy, m.jy * uy);
+  const float azz = fmaf(om1, m.pzz, m.jz * uz);
+  const float axy = fmaf(m.jx, uy, qxy), axz = fmaf(m.jx, uz, qxz), ayz = fmaf(m.jy, uz, qyz);
+  float axyy = 0.f, axzz = 0.f, axxy = 0.f, ayzz = 0.f, axxz = 0.f, ayyz = 0.f;
+  if (ORDER3) {
+    axyy = fmaf(ux, ayy, 2.0f * uy * qxy);
+    axzz = fmaf(ux, azz, 2.0f * uz * qxz);
+    axxy = fmaf(uy, axx, 2.0f * ux * qxy);
+    ayzz = fmaf(uy, azz, 2.0f * uz * qyz);
+    axxz = fmaf(uz, axx, 2.0f * ux * qxz);
+    ayyz = fmaf(uz, ayy, 2.0f * uy * qyz);
+  }
+  const float base = fmaf(-1.5f, (axx + ayy) + azz, m.drho);
+  const float jx3 = 3.0f * m.jx, jy3 = 3.0f * m.jy, jz3 = 3.0f * m.jz;
+  // edges of the plane (a, b): w_edge (e + 9 s t A_ab + s U + t V)
+  auto edges = [](float e, float ab9, float U, float V, float &pp, float &pm, float &mp,
+                  float &mm) {
+    constexpr float w2 = 1.0f / 36.0f;
+    const float ep = e + ab9, em = e - ab9;
+    pp = w2 * (ep + (U + V));
+    mm = w2 * (ep - (U + V));
+    pm = w2 * (em + (U - V));
+    mp = w2 * (em - (U - V));
+  };
+  // (x, y): (+,+) 13, (+,-) 7, (-,+) 11, (-,-) 5
+  edges(fmaf(4.5f, axx + ayy, base), 9.0f * axy,
+        fmaf(9.0f, axyy, jx3), fmaf(9.0f, axxy, jy3),
+        f[13], f[7], f[11], f[5]);
+  // (x, z): (+,+) 17, (+,-) 3, (-,+) 15, (-,-) 1
+  edges(fmaf(4.5f, axx + azz, base), 9.0f * axz,
+        fmaf(9.0f, axzz, jx3), fmaf(9.0f, axxz, jz3),
+        f[17], f[3], f[15], f[1]);
+  // (y, z): (+,+) 18, (+,-) 4, (-,+) 14, (-,-) 0
+  edges(fmaf(4.5f, ayy + azz, base), 9.0f * ayz,
+        fmaf(9.0f, ayzz, jy3), fmaf(9.0f, ayyz, jz3),
+        f[18], f[4], f[14], f[0]);
+  // faces: even part w_face (base + 9/2 A_aa), odd part closing j_a
+  constexpr float w1 = 1.0f / 18.0f;
+  const float ex = ((f[13] + f[7]) + (f[17] + f[3])) - ((f[11] + f[5]) + (f[15] + f[1]));
+  const float ey = ((f[13] + f[11]) + (f[18] + f[4])) - ((f[7] + f[5]) + (f[14] + f[0]));
+  const float ez = ((f[17] + f[15]) + (f[18] + f[14])) - ((f[3] + f[1]) + (f[4] + f[0]));
+  const float sx = w1 * fmaf(4.5f, axx, base), hx = 0.5f * (m.jx - ex);
+  const float sy = w1 * fmaf(4.5f, ayy, base), hy = 0.5f * (m.jy - ey);
+  const float sz = w1 * fmaf(4.5f, azz, base), hz = 0.5f * (m.jz - ez);
+  f[10] = sx + hx;
+  f[8] = sx - hx;
+  f[12] = sy + hy;
+  f[6] = sy - hy;
+  f[16] = sz + hz;
+  f[2] = sz - hz;
+  // rest: closes the mass
+  const float e4 = ((f[0] + f[1]) + (f[3] + f[4])) + ((f[14] + f[15]) + (f[17] + f[18]));
+  const float e8 = e4 + ((f[5] + f[7]) + (f[11] + f[13]));
+  const float fa = ((f[2] + f[6]) + (f[8] + f[10])) + (f[12] + f[16]);
+  f[9] = m.drho - (e8 + fa);
+}
+
+template <>
+struct Lattice<19> {
+  static constexpr int D = 3;
+  template <bool G = false>
+  __device__ __forceinline__ static Macro moments(const float (&f)[19]) {
+    static_assert(!G, "D3Q19 runs on shifted populations df only");
+    return moments_d3q19(f);
+  }
+  template <int MODEL, bool G = false>
+  __device__ __forceinline__ static void synth(const Macro &m, float om1, float (&f)[19]) {
+    static_assert(!G, "D3Q19 runs on shifted populations df only");
+    if (MODEL == 2) {  // the model's full equilibrium, then relax
+      float eq[19];
+      synth_d3q19<true>(m, 0.0f, eq);
+#pragma unroll
+      for (int i = 0; i < 19; ++i) f[i] = fmaf(1.0f - om1, eq[i] - f[i], f[i]);
+      return;
+    }
+    synth_d3q19<MODEL == 0>(m, om1, f);
+  }
+};
 
 // Grid geometry passed by value to every kernel. walls: bit a set = axis a
 // is bounded by no-slip walls through its first and last node planes
@@ -422,7 +591,7 @@ template <int Q>
 __host__ __device__ constexpr uint32_t vel_mask(int a, int s) {
   uint32_t m = 0;
   for (int i = 0; i < Q; ++i)
-    if (vel(i, a) == s) m |= 1u << i;
+    if (vel_q<Q>(i, a) == s) m |= 1u << i;
   return m;
 }
 
@@ -463,7 +632,6 @@ __device__ __forceinline__ uint32_t opposite_mask(uint32_t m) {
 // set to equilibrium, w_i (rho - 1), with rho closing the mass balance.
 template <int Q>
 __device__ __forceinline__ void wall_fill(uint32_t unknown, float (&df)[Q]) {
-  constexpr int D = Lattice<Q>::D;
   const uint32_t buried = unknown & opposite_mask<Q>(unknown);
 #pragma unroll
   for (int i = 0; i < Q; ++i)
@@ -473,14 +641,14 @@ __device__ __forceinline__ void wall_fill(uint32_t unknown, float (&df)[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if ((buried >> i) & 1u)
-        wb += weight<D>(i);
+        wb += weight_q<Q>(i);
       else
         s += df[i];
     }
     const float drho = s / (1.f - wb);
 #pragma unroll
     for (int i = 0; i < Q; ++i)
-      if ((buried >> i) & 1u) df[i] = weight<D>(i) * drho;
+      if ((buried >> i) & 1u) df[i] = weight_q<Q>(i) * drho;
   }
 }
 
@@ -508,14 +676,14 @@ __device__ __forceinline__ void load_logical(const typename Storage<S>::T *__res
   if (parity == 0) {
     const long long cell = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) df[i] = Storage<S>::template load<D>(f + i * n + cell, i);
+    for (int i = 0; i < Q; ++i) df[i] = Storage<S>::template load<Q>(f + i * n + cell, i);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int xs = wrap_add(x, -vel(i, 0), g.nx), ys = wrap_add(y, -vel(i, 1), g.ny);
-      const int zs = D == 3 ? wrap_add(z, -vel(i, 2), g.nz) : 0;
+      const int xs = wrap_add(x, -vel_q<Q>(i, 0), g.nx), ys = wrap_add(y, -vel_q<Q>(i, 1), g.ny);
+      const int zs = D == 3 ? wrap_add(z, -vel_q<Q>(i, 2), g.nz) : 0;
       const long long src = ((long long)zs * g.ny + ys) * g.nx + xs;
-      df[i] = Storage<S>::template load<D>(f + (Q - 1 - i) * n + src, i);
+      df[i] = Storage<S>::template load<Q>(f + (Q - 1 - i) * n + src, i);
     }
   }
 }

@@ -27,7 +27,7 @@ cudaError_t launch_step_walls(int q, int storage, int model, void *f, const Grid
 
 // The persistent row kernel for 16-bit stores (lbrr_step16.cu): sets
 // launched = false, launching nothing, where it does not apply (nx not a
-// multiple of 16, nx < 64, nx above 1024 (D3Q27) or 2048 (D2Q9), or no
+// multiple of 16, nx < 64, nx above 1024 (D3Q27, D3Q19) or 2048 (D2Q9), or no
 // block fits on an SM).
 cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid &g, float om1,
                               int parity, int *status, cudaStream_t st, bool &launched);

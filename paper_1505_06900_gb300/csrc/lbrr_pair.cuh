@@ -326,6 +326,122 @@ __device__ __forceinline__ void coeffs_reg2_27(const Macro2 &m, V (&c)[3][3][3])
   c[0][1][1] = fma(m.jy, m.uz, m.pyz);
 }
 
+// ----------------------------------------------------------------- D3Q19 --
+// Direction order of q19_to_q27: planes z = -1 (0..4) and z = +1 (14..18)
+// hold the crosses (0,-1), (-1,0), (0,0), (1,0), (0,1) (edges and one
+// face), plane z = 0 (5..13) the full 3x3 set. With g = df / w the weights
+// 1/3 : 1/18 : 1/36 enter the sums as 12 : 2 : 1, so the moments come out
+// multiplied by 36. The conserved ones (rho - 1, rho u) are divided by 36
+// (correctly rounded) rather than multiplied by the rounding of 1/36, which
+// would scale them by 1 + 7.5e-9 at every update.
+__device__ __forceinline__ Macro2 moments19(const V (&f)[19], float om1) {
+  const V mxx = add(f[1], f[3]), myy = add(f[0], f[4]);
+  const V m0 = fmas(2.0f, f[2], add(mxx, myy));
+  const V mx = sub(f[3], f[1]), my = sub(f[4], f[0]);
+  const V pxx = add(f[15], f[17]), pyy = add(f[14], f[18]);
+  const V p0 = fmas(2.0f, f[16], add(pxx, pyy));
+  const V px = sub(f[17], f[15]), py = sub(f[18], f[14]);
+  // plane z = 0: edges 5, 7, 11, 13; faces 8, 10 (x) and 6, 12 (y); rest 9
+  const V e57 = add(f[5], f[7]), e1113 = add(f[11], f[13]);
+  const V ee = add(e57, e1113);
+  const V fxx = add(f[8], f[10]), fyy = add(f[6], f[12]);
+  const V cxx = fmas(2.0f, fxx, ee), cyy = fmas(2.0f, fyy, ee);
+  const V c00 = fmas(12.0f, f[9], fmas(2.0f, fyy, cxx));
+  const V cx = fmas(2.0f, sub(f[10], f[8]), sub(add(f[7], f[13]), add(f[5], f[11])));
+  const V cy = fmas(2.0f, sub(f[12], f[6]), sub(e1113, e57));
+  const V cxy = sub(add(f[5], f[13]), add(f[7], f[11]));
+  auto div36 = [](V v) { return make_float2(v.x / 36.0f, v.y / 36.0f); };
+  const float k = 1.0f / 36.0f;
+  return macro(1.0f, om1, div36(add(c00, add(m0, p0))), div36(add(cx, add(mx, px))),
+               div36(add(cy, add(my, py))), div36(sub(p0, m0)),
+               scale(k, add(cxx, add(mxx, pxx))), scale(k, add(cyy, add(myy, pyy))),
+               scale(k, add(p0, m0)), scale(k, cxy), scale(k, sub(px, mx)),
+               scale(k, sub(py, my)), true);
+}
+
+// Post-collision g of a D3Q19 pair on the kept basis (orders 0-2 and the
+// sums / differences H_aab +- H_bcc of order 3), as synth_d3q19 of
+// lbrr_device.cuh with the weights divided out: A_ab = j_a u_b + P_ab,
+// A_abb = u_a A_bb + 2 u_b P_ab (P = om1 Pi), and per class of velocity
+//   rest  base = drho - 3/2 tr A
+//   face  base + 9/2 A_aa + s (3 j_a - 9 (A_abb + A_acc))
+//   edge  base + 9/2 (A_aa + A_bb) + 9 s t A_ab + s (3 j_a + 9 A_abb)
+//              + t (3 j_b + 9 A_aab).
+// ORDER3 = false: the order-2 regularized comparator. EQ: P = 0 (the
+// equilibrium), whose products by zero are left out.
+template <bool ORDER3, bool EQ>
+__device__ __forceinline__ void synth19(const Macro2 &m, V (&f)[19]) {
+  const V ux = m.ux, uy = m.uy, uz = m.uz;
+  V axx, ayy, azz, axy, axz, ayz;
+  if (EQ) {
+    axx = mul(m.jx, ux);
+    ayy = mul(m.jy, uy);
+    azz = mul(m.jz, uz);
+    axy = mul(m.jx, uy);
+    axz = mul(m.jx, uz);
+    ayz = mul(m.jy, uz);
+  } else {
+    axx = fma(m.jx, ux, m.pxx);
+    ayy = fma(m.jy, uy, m.pyy);
+    azz = fma(m.jz, uz, m.pzz);
+    axy = fma(m.jx, uy, m.pxy);
+    axz = fma(m.jx, uz, m.pxz);
+    ayz = fma(m.jy, uz, m.pyz);
+  }
+  const V jx3 = scale(3.0f, m.jx), jy3 = scale(3.0f, m.jy), jz3 = scale(3.0f, m.jz);
+  V ux_ = jx3, uy_ = jy3, uz_ = jz3;              // 3 j_a - 9 (A_abb + A_acc) (faces)
+  V exy_x = jx3, exy_y = jy3, exz_x = jx3, exz_z = jz3, eyz_y = jy3, eyz_z = jz3;
+  if (ORDER3) {
+    V axyy, axzz, axxy, ayzz, axxz, ayyz;
+    if (EQ) {
+      axyy = mul(ux, ayy);
+      axzz = mul(ux, azz);
+      axxy = mul(uy, axx);
+      ayzz = mul(uy, azz);
+      axxz = mul(uz, axx);
+      ayyz = mul(uz, ayy);
+    } else {
+      const V ux2 = add(ux, ux), uy2 = add(uy, uy), uz2 = add(uz, uz);
+      axyy = fma(ux, ayy, mul(uy2, m.pxy));
+      axzz = fma(ux, azz, mul(uz2, m.pxz));
+      axxy = fma(uy, axx, mul(ux2, m.pxy));
+      ayzz = fma(uy, azz, mul(uz2, m.pyz));
+      axxz = fma(uz, axx, mul(ux2, m.pxz));
+      ayyz = fma(uz, ayy, mul(uy2, m.pyz));
+    }
+    ux_ = fmas(-9.0f, add(axyy, axzz), jx3);
+    uy_ = fmas(-9.0f, add(axxy, ayzz), jy3);
+    uz_ = fmas(-9.0f, add(axxz, ayyz), jz3);
+    exy_x = fmas(9.0f, axyy, jx3);
+    exy_y = fmas(9.0f, axxy, jy3);
+    exz_x = fmas(9.0f, axzz, jx3);
+    exz_z = fmas(9.0f, axxz, jz3);
+    eyz_y = fmas(9.0f, ayzz, jy3);
+    eyz_z = fmas(9.0f, ayyz, jz3);
+  }
+  const V base = fmas(-1.5f, add(add(axx, ayy), azz), m.drho);
+  f[9] = base;
+  const V fx = fmas(4.5f, axx, base), fy = fmas(4.5f, ayy, base), fz = fmas(4.5f, azz, base);
+  f[10] = add(fx, ux_);
+  f[8] = sub(fx, ux_);
+  f[12] = add(fy, uy_);
+  f[6] = sub(fy, uy_);
+  f[16] = add(fz, uz_);
+  f[2] = sub(fz, uz_);
+  // edges of the plane (a, b): (+,+), (+,-), (-,+), (-,-)
+  auto edges = [](V e, V ab, V U, V W, V &pp, V &pm, V &mp, V &mm) {
+    const V ep = fmas(9.0f, ab, e), em = fmas(-9.0f, ab, e);
+    const V s = add(U, W), d = sub(U, W);
+    pp = add(ep, s);
+    mm = sub(ep, s);
+    pm = add(em, d);
+    mp = sub(em, d);
+  };
+  edges(fmas(4.5f, add(axx, ayy), base), axy, exy_x, exy_y, f[13], f[7], f[11], f[5]);
+  edges(fmas(4.5f, add(axx, azz), base), axz, exz_x, exz_z, f[17], f[3], f[15], f[1]);
+  edges(fmas(4.5f, add(ayy, azz), base), ayz, eyz_y, eyz_z, f[18], f[4], f[14], f[0]);
+}
+
 // Post-collision g of two cells in place. MODEL 0: RR, 1: order-2
 // regularized, 2: BGK g + (1 - om1)(g_eq - g).
 template <int Q, int MODEL>
@@ -370,6 +486,22 @@ __device__ __forceinline__ void collide<27, 2>(V (&f)[27], float om1) {
   synth27(c, eq);
 #pragma unroll
   for (int i = 0; i < 27; ++i) f[i] = fmas(1.0f - om1, sub(eq[i], f[i]), f[i]);
+}
+
+template <>
+__device__ __forceinline__ void collide<19, 0>(V (&f)[19], float om1) {
+  synth19<true, false>(moments19(f, om1), f);
+}
+template <>
+__device__ __forceinline__ void collide<19, 1>(V (&f)[19], float om1) {
+  synth19<false, false>(moments19(f, om1), f);
+}
+template <>
+__device__ __forceinline__ void collide<19, 2>(V (&f)[19], float om1) {
+  V eq[19];
+  synth19<true, true>(moments19(f, 0.0f), eq);
+#pragma unroll
+  for (int i = 0; i < 19; ++i) f[i] = fmas(1.0f - om1, sub(eq[i], f[i]), f[i]);
 }
 
 }  // namespace pair

@@ -68,7 +68,7 @@ int scratch_address(double **out) {
 extern "C" int lb_diagnostics_static(int lattice, int nx, int ny, int nz, int storage, int parity,
                                      const void *store, double *out, void *stream) {
   if (!store || !out) return lbrr::report_error(LB_EINVAL, "lb_diagnostics_static: null pointer");
-  if (lattice != LB_D2Q9 && lattice != LB_D3Q27)
+  if (lattice != LB_D2Q9 && lattice != LB_D3Q19 && lattice != LB_D3Q27)
     return lbrr::report_error(LB_EINVAL, "lb_diagnostics_static: unknown lattice %d", lattice);
   if (nx < 1 || ny < 1 || nz < 1 || (lattice == LB_D2Q9 && nz != 1))
     return lbrr::report_error(LB_EINVAL, "lb_diagnostics_static: bad grid %d x %d x %d", nx, ny,

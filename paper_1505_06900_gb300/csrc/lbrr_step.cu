@@ -37,11 +37,11 @@ __global__ void __launch_bounds__(kStepThreads)
   if (PARITY == 0) {
     const long long cell = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) df[i] = St::template load<D>(f + i * n + cell, i);
+    for (int i = 0; i < Q; ++i) df[i] = St::template load<Q>(f + i * n + cell, i);
     const Macro m = L::moments(df);
     L::template synth<MODEL>(m, om1, df);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) St::template store<D>(f + (Q - 1 - i) * n + cell, i, df[i]);
+    for (int i = 0; i < Q; ++i) St::template store<Q>(f + (Q - 1 - i) * n + cell, i, df[i]);
   } else {
     const int xs[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
     const int ys[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
@@ -58,18 +58,20 @@ __global__ void __launch_bounds__(kStepThreads)
     // gather: population i of x lives in slot opp(i) of x - xi_i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int cx = vel(i, 0), cy = vel(i, 1), cz = (D == 3) ? vel(i, 2) : 0;
+      const int cx = vel_q<Q>(i, 0), cy = vel_q<Q>(i, 1);
+      const int cz = (D == 3) ? vel_q<Q>(i, 2) : 0;
       const long long src = row(1 - cy, 1 - cz) + xs[1 - cx];
-      df[i] = St::template load<D>(f + (Q - 1 - i) * n + src, i);
+      df[i] = St::template load<Q>(f + (Q - 1 - i) * n + src, i);
     }
     const Macro m = L::moments(df);
     L::template synth<MODEL>(m, om1, df);
     // scatter: population i goes to slot i of x + xi_i
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int cx = vel(i, 0), cy = vel(i, 1), cz = (D == 3) ? vel(i, 2) : 0;
+      const int cx = vel_q<Q>(i, 0), cy = vel_q<Q>(i, 1);
+      const int cz = (D == 3) ? vel_q<Q>(i, 2) : 0;
       const long long dst = row(1 + cy, 1 + cz) + xs[1 + cx];
-      St::template store<D>(f + i * n + dst, i, df[i]);
+      St::template store<Q>(f + i * n + dst, i, df[i]);
     }
   }
 }
@@ -117,8 +119,9 @@ cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, f
     cudaError_t e = launch_step_row16(q, storage, model, f, g, om1, parity, status, st, launched);
     if (e != cudaSuccess || launched) return e;
   }
-  return q == 9 ? step_s<9>(storage, model, f, g, om1, parity, st)
-                : step_s<27>(storage, model, f, g, om1, parity, st);
+  if (q == 9) return step_s<9>(storage, model, f, g, om1, parity, st);
+  if (q == 19) return step_s<19>(storage, model, f, g, om1, parity, st);
+  return step_s<27>(storage, model, f, g, om1, parity, st);
 }
 
 }  // namespace lbrr

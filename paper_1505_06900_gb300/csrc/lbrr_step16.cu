@@ -66,6 +66,33 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// Slots of the Q-velocity lattice with cx = -1 (and, mirrored, cx = +1):
+// shifted_slot<Q>(k, pos) is the k-th slot with cx = +1 (pos) or -1, of the
+// shifted_slots<Q>() of each sign.
+template <int Q>
+__host__ __device__ constexpr int shifted_slots() { return Q == 19 ? 5 : Q / 3; }
+template <int Q>
+__host__ __device__ constexpr int shifted_slot(int k, bool pos) {
+  // D2Q9 / D3Q27: 3k (cx = -1), 3k + 2 (cx = +1); D3Q19: 1, 5, 8, 11, 15 and
+  // 3, 7, 10, 13, 17
+  return Q == 19 ? (pos ? 3 : 1) + 3 * k + (k >= 1) + (k >= 4) : 3 * k + (pos ? 2 : 0);
+}
+template <int Q>
+constexpr bool shifted_slots_ok() {
+  int np = 0, nm = 0;
+  for (int i = 0; i < Q; ++i) {
+    np += vel_q<Q>(i, 0) == 1;
+    nm += vel_q<Q>(i, 0) == -1;
+  }
+  if (np != shifted_slots<Q>() || nm != shifted_slots<Q>()) return false;
+  for (int k = 0; k < shifted_slots<Q>(); ++k)
+    if (vel_q<Q>(shifted_slot<Q>(k, true), 0) != 1 || vel_q<Q>(shifted_slot<Q>(k, false), 0) != -1)
+      return false;
+  return true;
+}
+static_assert(shifted_slots_ok<9>() && shifted_slots_ok<19>() && shifted_slots_ok<27>(),
+              "shifted-slot tables");
+
 template <int Q, int S, int MODEL, int PARITY, int TX>
 __global__ void __launch_bounds__(TX / 2)
     rr_step_tiled16_kernel(typename Storage<S>::T *__restrict__ f, const Grid g, const float om1) {
@@ -87,8 +114,8 @@ __global__ void __launch_bounds__(TX / 2)
   if (tid < Q) {
     int yy = y, zz = z;
     if (PARITY) {
-      yy = wrap_add(y, vel(tid, 1), g.ny);
-      zz = D == 3 ? wrap_add(z, vel(tid, 2), g.nz) : 0;
+      yy = wrap_add(y, vel_q<Q>(tid, 1), g.ny);
+      zz = D == 3 ? wrap_add(z, vel_q<Q>(tid, 2), g.nz) : 0;
     }
     srow[tid] = (long long)tid * n + ((long long)zz * g.ny + yy) * g.nx;
   }
@@ -126,7 +153,7 @@ __global__ void __launch_bounds__(TX / 2)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int s = PARITY ? Q - 1 - i : i;
-    const int sh = PARITY ? vel(i, 0) : 0;
+    const int sh = PARITY ? vel_q<Q>(i, 0) : 0;
     const T *p = &tile[s][c0 - sh];
     if (sh == 0)
       v[i] = Half<S>::to_f2(*reinterpret_cast<const T2 *>(p));
@@ -138,7 +165,7 @@ __global__ void __launch_bounds__(TX / 2)
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int s = PARITY ? i : Q - 1 - i;
-    const int sh = PARITY ? vel(i, 0) : 0;
+    const int sh = PARITY ? vel_q<Q>(i, 0) : 0;
     T *p = &tile[s][c0 + sh];
     if (sh == 0) {
       *reinterpret_cast<T2 *>(p) = Half<S>::from_f2(v[i]);
@@ -153,9 +180,9 @@ __global__ void __launch_bounds__(TX / 2)
   // tile positions [kHalo + cx_s, kHalo + TX + cx_s): whole 16-byte chunks
   // go out as vector stores, the 8 values per shifted slot that share a chunk
   // with a neighbouring segment one by one.
-  // Slots with cx = +1 are s % 3 == 2, with cx = -1 s % 3 == 0 (bit masks).
-  constexpr uint32_t kPosMask = Q == 27 ? 0x4924924u : 0x124u;
-  constexpr uint32_t kNegMask = Q == 27 ? 0x1249249u : 0x049u;
+  // Bit masks of the slots with cx = +1 and cx = -1.
+  constexpr uint32_t kPosMask = vel_mask<Q>(0, 1);
+  constexpr uint32_t kNegMask = vel_mask<Q>(0, -1);
   const uint32_t skip = !PARITY ? 0u
                                 : (kc == 0 ? kPosMask : 0u) | (kc == kInner - 1 ? kNegMask : 0u);
 #pragma unroll
@@ -166,14 +193,14 @@ __global__ void __launch_bounds__(TX / 2)
           *reinterpret_cast<const uint4 *>(&tile[s][kHalo + kChunk * kc]);
   }
   if (PARITY) {
-    // 8 values of each of the 2Q/3 shifted slots: item p -> shifted slot
-    // m = p / 8 (s = 3 (m / 2) for cx = -1, 3 (m / 2) + 2 for cx = +1), value t
-    constexpr int kEdgeItems = 2 * Q / 3 * kChunk;
+    // 8 values of each shifted slot: item p -> shifted slot m = p / 8 (the
+    // (m / 2)-th slot with cx = -1 for even m, with cx = +1 for odd m), value t
+    constexpr int kEdgeItems = 2 * shifted_slots<Q>() * kChunk;
 #pragma unroll
     for (int p = tid; p < kEdgeItems; p += kThreads) {
       const int m = p / kChunk, t = p % kChunk;
       const bool pos = m & 1;
-      const int s = 3 * (m >> 1) + (pos ? 2 : 0);
+      const int s = shifted_slot<Q>(m >> 1, pos);
       // cx = +1: positions kHalo+1 .. kHalo+7 and kHalo+TX
       // cx = -1: positions kHalo-1 and kHalo+TX-8 .. kHalo+TX-2
       const int j = pos ? (t < kChunk - 1 ? kHalo + 1 + t : kHalo + TX)
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(TX / 2)
 // waiting for the stores of the row before. Each (slot, row) pair is
 // read and written by exactly one row of the update, so rows never race.
 // Requires nx % 16 == 0 (16-byte rows), nx >= 64 (a thread per slot) and
-// nx / 2 threads per block (nx <= 1024 for D3Q27, 2048 for D2Q9).
+// nx / 2 threads per block (nx <= 1024 for D3Q27 and D3Q19, 2048 for D2Q9).
 
 constexpr uint32_t kRowWaitLimit = 1u << 24;
 
@@ -247,10 +274,10 @@ __device__ __forceinline__ void bulk_wait_all() {
   asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
 }
 
-// largest row (cells) of the row kernel: D3Q27 keeps <= 512 threads so that a
-// thread has the registers of a pair without spilling
+// largest row (cells) of the row kernel: D3Q27 and D3Q19 keep <= 512 threads
+// so that a thread has the registers of a pair without spilling
 template <int Q>
-constexpr int row16_max_nx() { return Q == 27 ? 1024 : 2048; }
+constexpr int row16_max_nx() { return Q == 9 ? 2048 : 1024; }
 
 // Row buffers in shared memory and how many rows ahead the copies run: the
 // buffer refilled for row k + kRowDist was last stored kRowBufs - kRowDist
@@ -297,8 +324,8 @@ __global__ void __launch_bounds__(row16_max_nx<Q>() / 2)
   auto slot_row = [&](int s, int r) -> T * {
     int y = r % g.ny, z = r / g.ny;
     if (PARITY) {
-      y = wrap_add(y, vel(s, 1), g.ny);
-      z = D == 3 ? wrap_add(z, vel(s, 2), g.nz) : 0;
+      y = wrap_add(y, vel_q<Q>(s, 1), g.ny);
+      z = D == 3 ? wrap_add(z, vel_q<Q>(s, 2), g.nz) : 0;
     }
     return f + (long long)s * g.n + ((long long)z * g.ny + y) * nx;
   };
@@ -348,7 +375,7 @@ __global__ void __launch_bounds__(row16_max_nx<Q>() / 2)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int s = PARITY ? Q - 1 - i : i;
-      const int sh = PARITY ? vel(i, 0) : 0;  // read at x - sh
+      const int sh = PARITY ? vel_q<Q>(i, 0) : 0;  // read at x - sh
       const T *p = t + (size_t)s * nx;
       if (sh == 0)
         v[i] = Half<S>::to_f2(*reinterpret_cast<const T2 *>(p + xa));
@@ -362,7 +389,7 @@ __global__ void __launch_bounds__(row16_max_nx<Q>() / 2)
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       const int s = PARITY ? i : Q - 1 - i;
-      const int sh = PARITY ? vel(i, 0) : 0;  // write at x + sh
+      const int sh = PARITY ? vel_q<Q>(i, 0) : 0;  // write at x + sh
       T *p = t + (size_t)s * nx;
       if (sh == 0) {
         *reinterpret_cast<T2 *>(p + xa) = Half<S>::from_f2(v[i]);
@@ -445,6 +472,9 @@ cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid
   if (q == 9)
     return storage == 1 ? row_m<9, 1>(model, f, g, om1, parity, status, st, launched)
                         : row_m<9, 2>(model, f, g, om1, parity, status, st, launched);
+  if (q == 19)
+    return storage == 1 ? row_m<19, 1>(model, f, g, om1, parity, status, st, launched)
+                        : row_m<19, 2>(model, f, g, om1, parity, status, st, launched);
   return storage == 1 ? row_m<27, 1>(model, f, g, om1, parity, status, st, launched)
                       : row_m<27, 2>(model, f, g, om1, parity, status, st, launched);
 }
@@ -483,6 +513,9 @@ cudaError_t launch_step_tiled16(int q, int storage, int model, void *f, const Gr
   if (q == 9)
     return storage == 1 ? tiled_m<9, 1>(model, f, g, om1, parity, st)
                         : tiled_m<9, 2>(model, f, g, om1, parity, st);
+  if (q == 19)
+    return storage == 1 ? tiled_m<19, 1>(model, f, g, om1, parity, st)
+                        : tiled_m<19, 2>(model, f, g, om1, parity, st);
   return storage == 1 ? tiled_m<27, 1>(model, f, g, om1, parity, st)
                       : tiled_m<27, 2>(model, f, g, om1, parity, st);
 }

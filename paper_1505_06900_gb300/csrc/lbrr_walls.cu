@@ -48,12 +48,13 @@ __global__ void __launch_bounds__(kWallThreads)
 
   if (PARITY == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) df[i] = St::template load<D>(f + i * n + cell, i);
+    for (int i = 0; i < Q; ++i) df[i] = St::template load<Q>(f + i * n + cell, i);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int cx = vel(i, 0), cy = vel(i, 1), cz = (D == 3) ? vel(i, 2) : 0;
-      df[i] = St::template load<D>(f + (Q - 1 - i) * n + row(1 - cy, 1 - cz) + xs[1 - cx], i);
+      const int cx = vel_q<Q>(i, 0), cy = vel_q<Q>(i, 1);
+      const int cz = (D == 3) ? vel_q<Q>(i, 2) : 0;
+      df[i] = St::template load<Q>(f + (Q - 1 - i) * n + row(1 - cy, 1 - cz) + xs[1 - cx], i);
     }
   }
   if (unknown) {
@@ -67,14 +68,15 @@ __global__ void __launch_bounds__(kWallThreads)
   }
   if (PARITY == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) St::template store<D>(f + (Q - 1 - i) * n + cell, i, df[i]);
+    for (int i = 0; i < Q; ++i) St::template store<Q>(f + (Q - 1 - i) * n + cell, i, df[i]);
   } else {
     const uint32_t outgoing = opposite_mask<Q>(unknown);  // destination beyond a wall
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if ((outgoing >> i) & 1u) continue;
-      const int cx = vel(i, 0), cy = vel(i, 1), cz = (D == 3) ? vel(i, 2) : 0;
-      St::template store<D>(f + i * n + row(1 + cy, 1 + cz) + xs[1 + cx], i, df[i]);
+      const int cx = vel_q<Q>(i, 0), cy = vel_q<Q>(i, 1);
+      const int cz = (D == 3) ? vel_q<Q>(i, 2) : 0;
+      St::template store<Q>(f + i * n + row(1 + cy, 1 + cz) + xs[1 + cx], i, df[i]);
     }
   }
 }
@@ -114,8 +116,9 @@ static cudaError_t walls_s(int storage, int model, void *f, const Grid &g, float
 
 cudaError_t launch_step_walls(int q, int storage, int model, void *f, const Grid &g, float om1,
                               int parity, cudaStream_t st) {
-  return q == 9 ? walls_s<9>(storage, model, f, g, om1, parity, st)
-                : walls_s<27>(storage, model, f, g, om1, parity, st);
+  if (q == 9) return walls_s<9>(storage, model, f, g, om1, parity, st);
+  if (q == 19) return walls_s<19>(storage, model, f, g, om1, parity, st);
+  return walls_s<27>(storage, model, f, g, om1, parity, st);
 }
 
 }  // namespace lbrr

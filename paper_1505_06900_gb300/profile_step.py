@@ -1,9 +1,9 @@
 """Small, self-contained run of the step kernel for profilers (ncu).
 
     python -m paper_1505_06900_gb300.profile_step [--n 256] [--storage f32|f16|bf16]
-                                                  [--lattice 27|9] [--steps 6]
+                                                  [--lattice 27|19|9] [--steps 6]
 
-Initialises a Taylor-Green vortex on an n^3 (D3Q27) or n^2 (D2Q9) periodic
+Initialises a Taylor-Green vortex on an n^3 (D3Q27, D3Q19) or n^2 (D2Q9) periodic
 grid, runs `steps` updates through the C ABI and prints the elapsed time. At
 n = 256 the D3Q27 FP32 store is 1.8 GB: larger than L2, small enough for a
 multi-pass profiler capture.
@@ -25,7 +25,7 @@ def main():
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--lattice", type=int, default=27, choices=[9, 27])
+    ap.add_argument("--lattice", type=int, default=27, choices=[9, 19, 27])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--closure", action="store_true",
@@ -34,7 +34,7 @@ def main():
     build_mod.build()
     storage = {"f32": B.STORE_F32, "f16": B.STORE_F16, "bf16": B.STORE_BF16}[args.storage]
     n = args.n
-    if args.lattice == 27:
+    if args.lattice != 9:
         shape = (n, n, n)
         rho, u = W.taylor_green_3d(n, 0.1)
         tau = W.taylor_green_3d_tau(n, 0.1)

@@ -1,5 +1,5 @@
-"""Parity at the benchmark's full size: D3Q27, FP32 store, 512^3 cells, the same
-kernels and launch configuration that bench.py times.
+"""Parity at the benchmark's full size: D3Q27 (and D3Q19), FP32 store, 512^3
+cells, the same kernels and launch configuration that bench.py times.
 
 The oracle cannot update 134M cells, so sampled cells are checked one by one:
 after one update the population i of cell x must equal the oracle's collision
@@ -19,16 +19,18 @@ N = 512
 TAU = W.taylor_green_3d_tau(N, 0.1, 1600.0)  # the benchmark's relaxation time
 
 
-def test_sampled_cells_at_512_cubed():
+@pytest.mark.parametrize("lattice", [O.D3Q27, O.D3Q19])
+def test_sampled_cells_at_512_cubed(lattice):
     from paper_1505_06900_gb300 import binding as B
-    c, w = O.lattice_tables(O.D3Q27)
+    c, w = O.lattice_tables(lattice)
+    q = len(w)
     free = torch.cuda.mem_get_info()[0]
-    need = 3 * 27 * N ** 3 * 4
+    need = 3 * q * N ** 3 * 4
     if free < need * 1.2:
         pytest.skip(f"needs {need / 1e9:.0f} GB of free device memory")
     gen = torch.Generator(device="cuda").manual_seed(1234)
-    wt = torch.tensor(w, dtype=torch.float32, device="cuda").view(27, 1, 1, 1)
-    df = torch.randn((27, N, N, N), generator=gen, device="cuda", dtype=torch.float32)
+    wt = torch.tensor(w, dtype=torch.float32, device="cuda").view(q, 1, 1, 1)
+    df = torch.randn((q, N, N, N), generator=gen, device="cuda", dtype=torch.float32)
     df.mul_(0.05 * wt)
     rng = np.random.default_rng(5)
     samples = [(0, 0, 0), (N - 1, N - 1, N - 1), (0, N - 1, 255), (N - 1, 0, 1), (300, 0, N - 1)]
@@ -41,11 +43,11 @@ def test_sampled_cells_at_512_cubed():
         iy = torch.tensor([(y + d) % N for d in range(-2, 3)], device="cuda")
         iz = torch.tensor([(z + d) % N for d in range(-2, 3)], device="cuda")
         sub = df.index_select(3, ix).index_select(2, iy).index_select(1, iz)
-        return sub.cpu().numpy().astype(np.float64) + w.reshape(27, 1, 1, 1)  # [27, z, y, x]
+        return sub.cpu().numpy().astype(np.float64) + w.reshape(q, 1, 1, 1)  # [Q, z, y, x]
 
     hoods = {s: hood(*s) for s in samples}
 
-    with B.Solver(B.D3Q27, (N, N, N), TAU) as s:
+    with B.Solver(lattice, (N, N, N), TAU) as s:
         s.set_populations(df)
         d0 = s.diagnostics()
         got = []
@@ -53,7 +55,7 @@ def test_sampled_cells_at_512_cubed():
             s.step(1)
             out = s.populations()
             idx = torch.tensor([[(z * N + y) * N + x for (x, y, z) in samples]], device="cuda")
-            got.append(out.view(27, -1).index_select(1, idx[0]).cpu().numpy().astype(np.float64))
+            got.append(out.view(q, -1).index_select(1, idx[0]).cpu().numpy().astype(np.float64))
             del out
             torch.cuda.empty_cache()
         d2 = s.diagnostics()
@@ -67,19 +69,19 @@ def test_sampled_cells_at_512_cubed():
         def post(dx, dy, dz):
             key = (dx, dy, dz)
             if key not in cache:
-                cache[key] = O.collide_cell(O.D3Q27, h[:, 2 + dz, 2 + dy, 2 + dx], TAU)
+                cache[key] = O.collide_cell(lattice, h[:, 2 + dz, 2 + dy, 2 + dx], TAU)
             return cache[key]
 
         # one update: f_i(x) = post(x - xi_i)_i
-        ref1 = np.array([post(-c[i, 0], -c[i, 1], -c[i, 2])[i] for i in range(27)]) - w
+        ref1 = np.array([post(-c[i, 0], -c[i, 1], -c[i, 2])[i] for i in range(q)]) - w
         assert np.max(np.abs(got[0][:, si] - ref1) / w) <= 1e-6, smp
 
         # two updates: f_i(x) = collide(f(x - xi_i, t+1))_i
-        ref2 = np.zeros(27)
-        for i in range(27):
+        ref2 = np.zeros(q)
+        for i in range(q):
             yx, yy, yz = -c[i, 0], -c[i, 1], -c[i, 2]
-            fy = np.array([post(yx - c[j, 0], yy - c[j, 1], yz - c[j, 2])[j] for j in range(27)])
-            ref2[i] = O.collide_cell(O.D3Q27, fy, TAU)[i] - w[i]
+            fy = np.array([post(yx - c[j, 0], yy - c[j, 1], yz - c[j, 2])[j] for j in range(q)])
+            ref2[i] = O.collide_cell(lattice, fy, TAU)[i] - w[i]
         assert np.max(np.abs(got[1][:, si] - ref2) / w) <= 1e-6, smp
 
     # conservation at full size

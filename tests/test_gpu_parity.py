@@ -27,7 +27,11 @@ CASES = [
     (O.D2Q9, (5, 3, 1)),
     (O.D3Q27, (150, 6, 5)),
     (O.D3Q27, (3, 4, 5)),
+    (O.D3Q19, (150, 6, 5)),
+    (O.D3Q19, (3, 4, 5)),
 ]
+# one case per lattice, several tiles with a ragged tail
+LARGE = [CASES[0], CASES[2], CASES[4]]
 
 
 def _cuda(a):
@@ -61,7 +65,7 @@ def test_steps_match_oracle(lattice, shape, collision):
             assert err <= ONE_STEP_TOL, (k, err)
 
 
-@pytest.mark.parametrize("lattice,shape", CASES[:3:2])
+@pytest.mark.parametrize("lattice,shape", LARGE)
 def test_moments_after_even_and_odd_updates(lattice, shape):
     d, _ = O.dims_of(lattice)
     tau = 0.75
@@ -79,7 +83,7 @@ def test_moments_after_even_and_odd_updates(lattice, shape):
             f = O.step(lattice, shape, tau, f, 1)
 
 
-@pytest.mark.parametrize("lattice,shape", CASES[:3:2])
+@pytest.mark.parametrize("lattice,shape", LARGE)
 @pytest.mark.parametrize("mode", [B.INIT_EQ, B.INIT_EQ_NEQ_FD])
 def test_init_matches_oracle(lattice, shape, mode):
     d, _ = O.dims_of(lattice)
@@ -107,23 +111,25 @@ def test_taylor_green_2d_1000_steps():
     assert rel_l2(r_g, r_o) <= 1e-6
 
 
-def test_taylor_green_3d_1000_steps():
-    """D3Q27 Taylor-Green vortex (Ma = 0.1, Re = 1600) on 24^3, 1000 updates."""
+@pytest.mark.parametrize("lattice", [O.D3Q27, O.D3Q19])
+def test_taylor_green_3d_1000_steps(lattice):
+    """3-D Taylor-Green vortex (Ma = 0.1, Re = 1600) on 24^3, 1000 updates."""
     n, mach = 24, 0.1
     tau = W.taylor_green_3d_tau(n, mach)
     rho, u = W.as_f32(*W.taylor_green_3d(n, mach))
     shape = (n, n, n)
-    with _solver(O.D3Q27, shape, tau) as s:
+    with _solver(lattice, shape, tau) as s:
         s.init_fields(_cuda(rho), _cuda(u))
         s.step(1000)
         r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
-    f = O.step(O.D3Q27, shape, tau, O.init(O.D3Q27, shape, tau, rho, u), 1000)
-    r_o, u_o, _ = O.fields(O.D3Q27, shape, f)
+    f = O.step(lattice, shape, tau, O.init(lattice, shape, tau, rho, u), 1000)
+    r_o, u_o, _ = O.fields(lattice, shape, f)
     assert rel_l2(u_g, u_o) <= 1e-5
     assert rel_l2(r_g, r_o) <= 1e-6
 
 
-@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (64, 48, 1)), (O.D3Q27, (20, 16, 12))])
+@pytest.mark.parametrize("lattice,shape", [(O.D2Q9, (64, 48, 1)), (O.D3Q27, (20, 16, 12)),
+                                           (O.D3Q19, (20, 16, 12))])
 def test_diagnostics_and_enstrophy(lattice, shape):
     d, _ = O.dims_of(lattice)
     rho, u = W.as_f32(*W.random_field(shape, d, seed=9, a_u=0.03))

@@ -27,7 +27,8 @@ VARIANT = {B.COLLIDE_RR: O.RR, B.COLLIDE_REG2: O.REG2, B.COLLIDE_BGK: O.BGK}
 # (lattice, shape, walls): closed boxes (edges and corners), channels, and
 # walls on other axes, with sizes that are not multiples of a block
 CASES = [(O.D2Q9, (12, 9, 1), 3), (O.D2Q9, (10, 7, 1), 2), (O.D2Q9, (7, 11, 1), 1),
-         (O.D3Q27, (8, 6, 5), 7), (O.D3Q27, (6, 7, 5), 2), (O.D3Q27, (5, 6, 7), 5)]
+         (O.D3Q27, (8, 6, 5), 7), (O.D3Q27, (6, 7, 5), 2), (O.D3Q27, (5, 6, 7), 5),
+         (O.D3Q19, (8, 6, 5), 7), (O.D3Q19, (5, 6, 7), 5)]
 
 
 def defined(lattice, shape, walls):
@@ -81,7 +82,7 @@ def test_walled_updates_match_the_oracle(lattice, shape, walls, collision, nstep
             assert np.all(u_g[(slice(None),) + tuple(first)] == 0.0)
 
 
-@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q27])
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q27, O.D3Q19])
 def test_channel_wave_decays_at_the_stokes_rate(lattice):
     """u_x = sin(pi y / H) between walls decays at nu pi^2 / H^2 (closed form)."""
     H, tau = 32, 0.8

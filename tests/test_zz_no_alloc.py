@@ -32,6 +32,7 @@ def _static(lib, s, buf, parity, storage, stream):
     (B.D3Q27, (40, 30, 20), B.STORE_F32),
     (B.D2Q9, (300, 7, 1), B.STORE_F32),
     (B.D3Q27, (24, 16, 12), B.STORE_F16),
+    (B.D3Q19, (40, 30, 20), B.STORE_F32),
 ])
 def test_static_diagnostics_match_lb_diagnostics(lattice, shape, storage):
     import torch
