@@ -47,14 +47,28 @@ __device__ __forceinline__ void mom3(V a, V b, V c, V &s0, V &s1, V &s2) {
   s1 = sub(c, a);
 }
 
-// rho, rho u, u and om1 * Pi1 from the raw weighted moments (scaled by
-// 1 / k_inv: 36 in 2D, 216 in 3D) of g.
-__device__ __forceinline__ Macro2 macro(float k, float om1, V m0r, V jxr, V jyr, V jzr, V pxxr,
-                                        V pyyr, V pzzr, V pxyr, V pxzr, V pyzr, bool three_d) {
+// x / KDEN for the conserved moments: x k_hi + x k_lo, with k_hi the float32
+// rounding of 1 / KDEN and k_lo that of the remainder. The product with k_hi
+// alone would scale rho - 1 and rho u by k_hi KDEN = 1 + 7.5e-9 (KDEN = 36,
+// 216) at every update, a drift of mass and momentum that adds up over long
+// runs; the two-term form leaves one rounding and no systematic factor.
+template <int KDEN>
+__device__ __forceinline__ V div_k(V x) {
+  constexpr float hi = 1.0f / KDEN;
+  constexpr float lo = (float)(1.0 / KDEN - (double)hi);
+  return fma(x, bc(lo), scale(hi, x));
+}
+
+// rho, rho u, u and om1 * Pi1 from the raw weighted moments (KDEN times the
+// moments: 36 for D2Q9 and D3Q19, 216 for D3Q27) of g.
+template <int KDEN>
+__device__ __forceinline__ Macro2 macro(float om1, V m0r, V jxr, V jyr, V jzr, V pxxr, V pyyr,
+                                        V pzzr, V pxyr, V pxzr, V pyzr, bool three_d) {
+  constexpr float k = 1.0f / KDEN;
   Macro2 m;
-  m.drho = scale(k, m0r);
-  m.jx = scale(k, jxr);
-  m.jy = scale(k, jyr);
+  m.drho = div_k<KDEN>(m0r);
+  m.jx = div_k<KDEN>(jxr);
+  m.jy = div_k<KDEN>(jyr);
   m.rho = add(bc(1.0f), m.drho);
   // u = j / rho correctly rounded, lane by lane (as the scalar form does)
   m.ux = make_float2(m.jx.x / m.rho.x, m.jx.y / m.rho.y);
@@ -66,7 +80,7 @@ __device__ __forceinline__ Macro2 macro(float k, float om1, V m0r, V jxr, V jyr,
   m.pyy = fmas(ok, pyyr, scale(no, fma(m.jy, m.uy, c0)));
   m.pxy = fmas(ok, pxyr, scale(no, mul(m.jx, m.uy)));
   if (three_d) {
-    m.jz = scale(k, jzr);
+    m.jz = div_k<KDEN>(jzr);
     m.uz = make_float2(m.jz.x / m.rho.x, m.jz.y / m.rho.y);
     m.pzz = fmas(ok, pzzr, scale(no, fma(m.jz, m.uz, c0)));
     m.pxz = fmas(ok, pxzr, scale(no, mul(m.jx, m.uz)));
@@ -87,7 +101,7 @@ __device__ __forceinline__ Macro2 moments9(const V (&f)[9], float om1) {
   mom3(s1[0], s1[1], s1[2], m10, m11, m12);
   mom3(s2[0], s2[1], s2[2], m20, m21, m22);
   const V z = bc(0.0f);
-  return macro(1.0f / 36.0f, om1, m00, m10, m01, z, m20, m02, z, m11, z, z, false);
+  return macro<36>(om1, m00, m10, m01, z, m20, m02, z, m11, z, z, false);
 }
 
 // one-dimensional synthesis with the weight divided out
@@ -162,8 +176,7 @@ __device__ __forceinline__ Macro2 moments27(const V (&f)[27], float om1) {
   mom3(y10[0], y10[1], y10[2], m100, m101, t[3]);
   mom3(y11[0], y11[1], y11[2], m110, t[4], t[5]);
   mom3(y20[0], y20[1], y20[2], m200, t[6], t[7]);
-  return macro(1.0f / 216.0f, om1, m000, m100, m010, m001, m200, m020, m002, m110, m101, m011,
-               true);
+  return macro<216>(om1, m000, m100, m010, m001, m200, m020, m002, m110, m101, m011, true);
 }
 
 __device__ __forceinline__ void synth27(const V (&c)[3][3][3], V (&f)[27]) {
@@ -331,9 +344,7 @@ __device__ __forceinline__ void coeffs_reg2_27(const Macro2 &m, V (&c)[3][3][3])
 // hold the crosses (0,-1), (-1,0), (0,0), (1,0), (0,1) (edges and one
 // face), plane z = 0 (5..13) the full 3x3 set. With g = df / w the weights
 // 1/3 : 1/18 : 1/36 enter the sums as 12 : 2 : 1, so the moments come out
-// multiplied by 36. The conserved ones (rho - 1, rho u) are divided by 36
-// (correctly rounded) rather than multiplied by the rounding of 1/36, which
-// would scale them by 1 + 7.5e-9 at every update.
+// multiplied by 36.
 __device__ __forceinline__ Macro2 moments19(const V (&f)[19], float om1) {
   const V mxx = add(f[1], f[3]), myy = add(f[0], f[4]);
   const V m0 = fmas(2.0f, f[2], add(mxx, myy));
@@ -350,13 +361,9 @@ __device__ __forceinline__ Macro2 moments19(const V (&f)[19], float om1) {
   const V cx = fmas(2.0f, sub(f[10], f[8]), sub(add(f[7], f[13]), add(f[5], f[11])));
   const V cy = fmas(2.0f, sub(f[12], f[6]), sub(e1113, e57));
   const V cxy = sub(add(f[5], f[13]), add(f[7], f[11]));
-  auto div36 = [](V v) { return make_float2(v.x / 36.0f, v.y / 36.0f); };
-  const float k = 1.0f / 36.0f;
-  return macro(1.0f, om1, div36(add(c00, add(m0, p0))), div36(add(cx, add(mx, px))),
-               div36(add(cy, add(my, py))), div36(sub(p0, m0)),
-               scale(k, add(cxx, add(mxx, pxx))), scale(k, add(cyy, add(myy, pyy))),
-               scale(k, add(p0, m0)), scale(k, cxy), scale(k, sub(px, mx)),
-               scale(k, sub(py, my)), true);
+  return macro<36>(om1, add(c00, add(m0, p0)), add(cx, add(mx, px)), add(cy, add(my, py)),
+                   sub(p0, m0), add(cxx, add(mxx, pxx)), add(cyy, add(myy, pyy)), add(p0, m0),
+                   cxy, sub(px, mx), sub(py, my), true);
 }
 
 // Post-collision g of a D3Q19 pair on the kept basis (orders 0-2 and the
