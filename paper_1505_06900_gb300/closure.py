@@ -172,6 +172,27 @@ def evaluate(net, n_fine: int, mach: float, re: float, seed: int, coarse_steps: 
     return out
 
 
+def held_out_loss(net, n_fine: int, mach: float, re: float, seed: int, snapshots) -> dict:
+    """A priori check on a phase the network was not trained on: the mean
+    square of the standardised targets (orders 3..6 that the recursion leaves
+    out) over every coarse cell of the filtered snapshots, left as they are
+    (the zero network, i.e. plain RR) and after subtracting the network's
+    prediction."""
+    import torch
+    raw = B.MLP()  # identity standardisation: raw targets
+    out_scale = torch.from_numpy(net.scaling[2].astype(np.float64)).cuda()
+    s_zero = s_net = 0.0
+    count = 0
+    for _, _, coarse in _snapshots(n_fine, mach, re, [seed], snapshots):
+        T = coarse.closure_targets(raw)[:, :17].double() / out_scale
+        Y = net.forward(coarse.closure_features(net))[:, :17].double()
+        s_zero += float((T * T).sum())
+        s_net += float(((Y - T) ** 2).sum())
+        count += T.numel()
+    raw.close()
+    return {"zero": s_zero / count, "trained": s_net / count, "values": count}
+
+
 def study(n_fine=64, mach=0.3, re=1600.0, train_seeds=range(1, 9), eval_seed=9,
           snapshots=(100, 200, 300, 400), fraction=0.25, steps=1500, batch=8192, lr=2e-3,
           coarse_steps=200):
