@@ -28,6 +28,7 @@ struct lb_ctx {
   float *fields = nullptr;     // lazily allocated (1 + d) * n floats for enstrophy / run_host
   float *mom = nullptr;        // lazily allocated 10 * n floats: moment field of the closure
   float *ystd = nullptr;       // lazily allocated 17 * n floats: the network's predictions
+                               // (grids the fused TMA-fed network does not take)
   void *xs = nullptr;          // feature source of the TMA-fed network (row-tile grids)
   CUtensorMap xs_map{};        // its tensor map
   const lb_mlp *closure = nullptr;  // learned closure in use (not owned)
@@ -280,12 +281,9 @@ int lb_step(lb_ctx *c, int n) {
       e = lbrr::launch_feature_source(c->closure->d, static_cast<const float *>(c->f), c->g,
                                       c->parity, c->xs, c->stream);
       if (e == cudaSuccess)
-        e = lbrr::launch_mlp_conv(c->closure->d, c->xs_map, c->g, c->ystd, c->closure->status,
-                                  c->closure->nblocks, c->stream);
-      if (e == cudaSuccess)
-        e = lbrr::launch_step_delta(c->closure->d, static_cast<float *>(c->f), c->g, om1,
-                                    c->parity, c->ystd, c->fallbacks, c->closure_bound,
-                                    c->stream);
+        e = lbrr::launch_mlp_conv_step(c->closure->d, c->xs_map, c->g, static_cast<float *>(c->f),
+                                       om1, c->parity, c->fallbacks, c->closure_bound,
+                                       c->closure->status, c->closure->nblocks, c->stream);
     } else if (c->closure) {
       e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
       if (e == cudaSuccess)
@@ -645,7 +643,8 @@ static int ensure_mom(lb_ctx *c, bool for_step) {
   const bool conv = for_step && lbrr::mlp_conv_supported(c->g);
   cudaError_t e = cudaSuccess;
   if (!conv && !c->mom) e = cudaMalloc(&c->mom, sizeof(float) * 10 * (size_t)c->g.n);
-  if (e == cudaSuccess && !c->ystd) e = cudaMalloc(&c->ystd, sizeof(float) * 17 * (size_t)c->g.n);
+  if (e == cudaSuccess && !conv && !c->ystd)  // the fused network writes no predictions
+    e = cudaMalloc(&c->ystd, sizeof(float) * 17 * (size_t)c->g.n);
   if (e == cudaSuccess && conv && !c->xs) {
     e = cudaMalloc(&c->xs, lbrr::feature_source_bytes(c->g));
     if (e == cudaSuccess) {

@@ -22,17 +22,6 @@ namespace {
 
 constexpr int kAux = 128;
 
-// (a, b, c) powers of the 17 high-order coefficients, in target order
-__host__ __device__ constexpr int hi_pow(int k, int axis) {
-  // packed as a + 3 b + 9 c
-  constexpr int code[17] = {2 + 3 * 1,     2 + 9 * 1,     1 + 3 * 2,     1 + 9 * 2,
-                            3 * 1 + 9 * 2, 3 * 2 + 9 * 1, 1 + 3 + 9,     2 + 3 * 2,
-                            2 + 9 * 2,     3 * 2 + 9 * 2, 1 + 3 + 9 * 2, 1 + 3 * 2 + 9,
-                            2 + 3 + 9,     2 + 3 + 9 * 2, 2 + 3 * 2 + 9, 1 + 3 * 2 + 9 * 2,
-                            2 + 3 * 2 + 9 * 2};
-  return axis == 0 ? code[k] % 3 : (axis == 1 ? (code[k] / 3) % 3 : code[k] / 9);
-}
-
 // --------------------------------------------------------------- moments --
 __global__ void __launch_bounds__(kAux)
     moment_field_kernel(const float *__restrict__ f, const Grid g, const int parity,
@@ -162,56 +151,11 @@ __global__ void __launch_bounds__(kDT)
   const int x = blockIdx.x * kDT + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
-  const long long n = g.n;
-  const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
-  const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
-  const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
-  auto cell_at = [&](int b, int c, int a) -> long long {
-    return ((long long)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
-  };
-  const long long cell = cell_at(1, 1, 1);
-  float df[27];
+  const long long cell = ((long long)z * g.ny + y) * g.nx + x;
+  float yk[kMlpOutUsed];
 #pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    if (PARITY == 0)
-      df[i] = f[i * n + cell];
-    else
-      df[i] = f[(26 - i) * n + cell_at(1 - vel(i, 1), 1 - vel(i, 2), 1 - vel(i, 0))];
-  }
-  const Macro m = Lattice<27>::moments(df);
-  float c[3][3][3];
-  coeffs_rr_d3q27(m, om1, c);
-  bool use = true;
-  float cc[3][3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) cc[a][b][q] = c[a][b][q];
-#pragma unroll
-  for (int k = 0; k < kMlpOutUsed; ++k) {
-    const float yk = __ldg(ystd + k * n + cell);
-    use = use && (fabsf(yk) <= bound);  // also false for NaN
-    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yk * p.out_scale[k]);
-  }
-  float out[27];
-  if (use) {
-    synth_tensor_d3q27<false>(cc, out);
-#pragma unroll
-    for (int i = 0; i < 27; ++i) use = use && (out[i] + weight<3>(i) > 0.0f);
-  }
-  if (!use) {
-    synth_tensor_d3q27<false>(c, out);
-    if (fallbacks) atomicAdd(fallbacks, 1ull);
-  }
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    if (PARITY == 0)
-      f[(26 - i) * n + cell] = out[i];
-    else
-      f[i * n + cell_at(1 + vel(i, 1), 1 + vel(i, 2), 1 + vel(i, 0))] = out[i];
-  }
+  for (int k = 0; k < kMlpOutUsed; ++k) yk[k] = __ldg(ystd + k * g.n + cell);
+  closure_update_cell<PARITY>(p, f, g, om1, x, y, z, yk, fallbacks, bound);
 }
 
 }  // namespace

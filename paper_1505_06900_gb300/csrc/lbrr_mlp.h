@@ -41,6 +41,78 @@ struct MlpDevice {
 
 __device__ void mlp_refresh_one(MlpDevice p, int k, float w);
 
+// (a, b, c) powers of x^a y^b z^c of the 17 high-order coefficients, in the
+// order of the network's outputs (xxy, xxz, xyy, xzz, yzz, yyz, xyz, xxyy,
+// xxzz, yyzz, xyzz, xyyz, xxyz, xxyzz, xxyyz, xyyzz, xxyyzz)
+__host__ __device__ constexpr int hi_pow(int k, int axis) {
+  // packed as a + 3 b + 9 c
+  constexpr int code[17] = {2 + 3 * 1,     2 + 9 * 1,     1 + 3 * 2,     1 + 9 * 2,
+                            3 * 1 + 9 * 2, 3 * 2 + 9 * 1, 1 + 3 + 9,     2 + 3 * 2,
+                            2 + 9 * 2,     3 * 2 + 9 * 2, 1 + 3 + 9 * 2, 1 + 3 * 2 + 9,
+                            2 + 3 + 9,     2 + 3 + 9 * 2, 2 + 3 * 2 + 9, 1 + 3 * 2 + 9 * 2,
+                            2 + 3 * 2 + 9 * 2};
+  return axis == 0 ? code[k] % 3 : (axis == 1 ? (code[k] / 3) % 3 : code[k] / 9);
+}
+
+// The closure update of cell (x, y, z) of an FP32 D3Q27 AA store (parity as
+// in lbrr_step.cu): the RR coefficients plus (1 - 1/tau) times the network's
+// correction, ystd[k] out_scale[k] added to coefficient k of orders 3..6;
+// plain RR for the cell (counted in *fallbacks) when a standardised
+// prediction exceeds the bound (or is not a number) or a corrected population
+// is not positive. Each cell reads exactly the locations it writes. IDX is
+// the type of the element offsets: int needs 27 N < 2^31 (fewer registers).
+template <int PARITY, typename IDX = long long>
+__device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *__restrict__ f,
+                                                    const Grid &g, const float om1, int x, int y,
+                                                    int z, const float (&ystd)[kMlpOutUsed],
+                                                    unsigned long long *fallbacks,
+                                                    const float bound) {
+  const IDX n = (IDX)g.n;
+  const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
+  const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
+  const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
+  auto cell_at = [&](int b, int c, int a) -> IDX {
+    return ((IDX)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
+  };
+  const IDX cell = cell_at(1, 1, 1);
+  float df[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (PARITY == 0)
+      df[i] = f[i * n + cell];
+    else
+      df[i] = f[(26 - i) * n + cell_at(1 - vel(i, 1), 1 - vel(i, 2), 1 - vel(i, 0))];
+  }
+  const Macro m = Lattice<27>::moments(df);
+  bool use = true;
+  float cc[3][3][3];
+  coeffs_rr_d3q27(m, om1, cc);
+#pragma unroll
+  for (int k = 0; k < kMlpOutUsed; ++k) {
+    const float yk = ystd[k];
+    use = use && (fabsf(yk) <= bound);  // also false for NaN
+    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yk * p.out_scale[k]);
+  }
+  float out[27];
+  if (use) {
+    synth_tensor_d3q27<false>(cc, out);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) use = use && (out[i] + weight<3>(i) > 0.0f);
+  }
+  if (!use) {  // plain RR: the coefficients again from the moments (rare)
+    coeffs_rr_d3q27(m, om1, cc);
+    synth_tensor_d3q27<false>(cc, out);
+    if (fallbacks) atomicAdd(fallbacks, 1ull);
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (PARITY == 0)
+      f[(26 - i) * n + cell] = out[i];
+    else
+      f[i * n + cell_at(1 + vel(i, 1), 1 + vel(i, 2), 1 + vel(i, 0))] = out[i];
+  }
+}
+
 size_t mlp_train_smem();
 
 // Forward (T == nullptr: writes Y [M][32]) or forward + backward (writes the
@@ -75,14 +147,20 @@ cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, c
 // The TMA-fed, pipelined forward pass (lbrr_mlp_conv.cu) for grids whose
 // rows are whole 128-cell tiles: the feature source xs (standardised moments,
 // BF16, 16 channels, one-cell periodic halo: feature_source_bytes(g) bytes),
-// its tensor map, and the network on it writing Y [17][N].
+// its tensor map, and the network on it.
 bool mlp_conv_supported(const Grid &g);
 size_t feature_source_bytes(const Grid &g);
 cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map);
 cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid &g, int parity,
                                   void *xs, cudaStream_t st);
-cudaError_t launch_mlp_conv(const MlpDevice &p, const CUtensorMap &map, const Grid &g, float *Y,
-                            int *status, int nblocks, cudaStream_t st);
+// The network fused with the closure update: the thread that owns a
+// tile row takes its cell's 17 predictions from the layer-3 accumulator and
+// updates the cell in place (closure_update_cell), so no prediction goes
+// through device memory. On a timeout (*status = 1) part of the cells have
+// not been updated.
+cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
+                                 float *f, float om1, int parity, unsigned long long *fallbacks,
+                                 float bound, int *status, int nblocks, cudaStream_t st);
 // One update of an FP32 D3Q27 store with the learned correction: ystd [17][N]
 // holds the network's standardised predictions for the current populations.
 cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,

@@ -1,5 +1,6 @@
-// Closure-network forward pass for grids whose rows are whole 128-cell tiles,
-// fed by the tensor memory accelerator (TMA) and pipelined across tiles.
+// Closure-network forward pass fused with the closure update, for grids whose
+// rows are whole 128-cell tiles, fed by the tensor memory accelerator (TMA)
+// and pipelined across tiles.
 //
 // Layer 1 of the network is a 3x3x3 convolution of the standardised moment
 // field: its 270 inputs for a cell are the 10 moments of the 27 cells around
@@ -21,8 +22,10 @@
 //   warps 2-17  four epilogue groups of four warps taking every fourth tile;
 //               each reads its layer-1 accumulator (thread = TMEM lane = tile
 //               row), applies bias and tanh, writes the BF16 hidden row,
-//               issues layers 2 and 3 itself and writes the 17 standardised
-//               outputs of its row.
+//               issues layers 2 and 3 itself and, with the 17 standardised
+//               outputs of its row, performs the closure update of that
+//               row's cell in the population store (closure_update_cell):
+//               the step of the learned closure is fused into the network.
 // Group g owns TMEM columns 128 g .. 128 g + 127: the first 64 take its
 // layer-1 accumulator (released as soon as the group has read it, so the
 // next tile's layer 1 can start), the other 64 its layer 2 and then layer 3.
@@ -145,9 +148,11 @@ __device__ __forceinline__ void load_acc32(uint32_t taddr, uint32_t (&v)[32]) {
   tmem_wait_ld();
 }
 
+template <int PARITY, typename IDX>
 __global__ void __launch_bounds__(kConvThreads, 1)
     mlp_conv_kernel(MlpDevice p, const __grid_constant__ CUtensorMap xs_map, const Grid g,
-                    float *__restrict__ Y, int *status) {
+                    float *__restrict__ f, const float om1, unsigned long long *fallbacks,
+                    const float bound, int *status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
@@ -348,10 +353,16 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       fence_after();
       load_acc32(lane_addr + c3, v);
       fence_before();
-      const long long cell = tile * kCRows + r;
+      // the closure update of this row's cell with its 17 predictions
       const float *b3 = sb + 2 * kMlpHidden;
+      float yk[kMlpOutUsed];
 #pragma unroll
-      for (int k = 0; k < kMlpOutUsed; ++k) Y[k * g.n + cell] = __uint_as_float(v[k]) + b3[k];
+      for (int k = 0; k < kMlpOutUsed; ++k) yk[k] = __uint_as_float(v[k]) + b3[k];
+      const uint32_t t = (uint32_t)tile, tpr = (uint32_t)g.nx / kCRows;
+      const uint32_t row = t / tpr;
+      const int x = (int)(t - row * tpr) * kCRows + r;
+      closure_update_cell<PARITY, IDX>(p, f, g, om1, x, (int)(row % (uint32_t)g.ny),
+                                       (int)(row / (uint32_t)g.ny), yk, fallbacks, bound);
     }
   }
 
@@ -444,16 +455,21 @@ cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_conv(const MlpDevice &p, const CUtensorMap &map, const Grid &g, float *Y,
-                            int *status, int nblocks, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(mlp_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kConvSmem);
+cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
+                                 float *f, float om1, int parity, unsigned long long *fallbacks,
+                                 float bound, int *status, int nblocks, cudaStream_t st) {
+  // 32-bit element offsets where every slot of the store is addressable so
+  auto kern = 27 * g.n < (1LL << 31) ? (parity ? mlp_conv_kernel<1, int> : mlp_conv_kernel<0, int>)
+                                     : (parity ? mlp_conv_kernel<1, long long>
+                                               : mlp_conv_kernel<0, long long>);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
   if (e != cudaSuccess) return e;
   const long long tiles = g.n / kCRows;
   if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
   const int nb = (int)(tiles < nblocks ? tiles : nblocks);
   if (nb < 1) return cudaSuccess;
-  mlp_conv_kernel<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, Y, status);
+  kern<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, f, om1, fallbacks, bound, status);
   return cudaGetLastError();
 }
 
