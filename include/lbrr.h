@@ -141,7 +141,12 @@ LB_API int lb_set_stream(lb_ctx *ctx, void *stream);
 LB_API int lb_init_fields(lb_ctx *ctx, const float *rho, const float *u, int init_mode);
 
 /* Advance n >= 0 full collide-and-stream updates (eq_discr_bgk_reg). n == 0 is
- * a no-op. Asynchronous on the context's stream. With a 16-bit store the
+ * a no-op. Asynchronous on the context's stream. Without a learned closure,
+ * runs of 8 updates are replayed from a CUDA graph that the context captures
+ * on first use (one per starting AA parity, on a stream of its own); the
+ * results are those of update-by-update launches, bit for bit. While the
+ * context's stream is being captured by the caller, updates are launched one
+ * by one into that capture. With a 16-bit store the
  * update waits (boundedly) for its own bulk copies; if such a wait ever
  * expires, the next lb_diagnostics or lb_get_state returns LB_ETIMEOUT. */
 LB_API int lb_step(lb_ctx *ctx, int n);

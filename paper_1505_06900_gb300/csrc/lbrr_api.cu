@@ -35,6 +35,11 @@ struct lb_ctx {
   float closure_bound = 0.f;
   unsigned long long *fallbacks = nullptr;  // device counter of cells that fell back to RR
   cudaStream_t stream = nullptr;
+  // CUDA graphs of kGraphSteps plain updates starting at parity 0 / 1 (built
+  // on first use, on a private capture stream, and replayed on `stream`)
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_off = false;  // capture failed once: launch update by update
   char err[512] = {0};
 };
 
@@ -90,6 +95,11 @@ struct DeviceGuard {
 };
 
 int free_all(lb_ctx *c) {
+  for (auto &ge : c->graph)
+    if (ge) cudaGraphExecDestroy(ge);
+  c->graph[0] = c->graph[1] = nullptr;
+  if (c->capture) cudaStreamDestroy(c->capture);
+  c->capture = nullptr;
   if (c->f) cudaFree(c->f);
   if (c->partials) cudaFree(c->partials);
   if (c->dout) cudaFree(c->dout);
@@ -270,11 +280,62 @@ int lb_init_fields(lb_ctx *c, const float *rho, const float *u, int init_mode) {
   return LB_OK;
 }
 
+namespace {
+
+// Updates per CUDA graph of plain (closure-free) updates; even, so a replay
+// leaves the AA parity as it found it.
+constexpr int kGraphSteps = 8;
+
+// The graph of kGraphSteps updates from the context's current parity, built
+// once: the same launches as the update-by-update path, recorded by stream
+// capture. Null (and never tried again) if the capture fails.
+cudaGraphExec_t step_graph(lb_ctx *c, float om1) {
+  const int p = c->parity;
+  if (c->graph[p] || c->graph_off) return c->graph[p];
+  cudaError_t e = cudaSuccess;
+  if (!c->capture) e = cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking);
+  cudaGraph_t graph = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && le == cudaSuccess; ++k)
+      le = lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, p ^ (k & 1),
+                             c->status, c->capture);
+    e = cudaStreamEndCapture(c->capture, &graph);
+    if (e == cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[p], graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    c->graph[p] = nullptr;
+    c->graph_off = true;
+  }
+  return c->graph[p];
+}
+
+}  // namespace
+
 int lb_step(lb_ctx *c, int n) {
   LB_CHECK_CTX(c);
   if (n < 0) return fail(c, LB_EINVAL, "negative step count %d", n);
   DeviceGuard dg(c->device);
   const float om1 = (float)(1.0 - 1.0 / c->tau);
+  // runs of plain updates replay a captured graph (one launch per
+  // kGraphSteps updates instead of one per update); not while the caller is
+  // capturing the context's stream into a graph of its own
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const bool capturing = cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess ||
+                         cs != cudaStreamCaptureStatusNone;
+  if (capturing) cudaGetLastError();
+  while (!c->closure && !capturing && n >= kGraphSteps) {
+    cudaGraphExec_t ge = step_graph(c, om1);
+    if (!ge) break;
+    cudaError_t e = cudaGraphLaunch(ge, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step graph launch");
+    c->steps += kGraphSteps;
+    n -= kGraphSteps;
+  }
   for (int k = 0; k < n; ++k) {
     cudaError_t e;
     if (c->closure && c->xs) {
