@@ -475,8 +475,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--n", type=int, default=512)
-    ap.add_argument("--cpu-sample", type=int, default=64)
-    ap.add_argument("--cpu-steps", type=int, default=30)
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--cpu-steps", type=int, default=50)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     args = ap.parse_args()
     if args.warmup < 3:
