@@ -300,6 +300,37 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
     }
 
 
+def shear_variant(B, torch, stream, peak_gbs, n: int = 2048, steps: int = 20000,
+                  machs=(0.1, 0.3, 0.5)):
+    """The periodic D2Q9 double shear layer at n^2 (Re 1000 on L = n), FP32 store: the
+    updates of a whole run timed with CUDA events on the solver's stream (lb_step
+    replays captured graphs of 8 updates), for each Mach number; the kinetic energy
+    at the end against the start (finite: the run stayed stable)."""
+    from paper_1505_06900_gb300 import workloads as W
+    out = {"grid": [n, n], "steps": steps, "re": 1000.0, "bytes_per_update": 72, "runs": {}}
+    for mach in machs:
+        rho, u = W.double_shear_2d(n, mach)
+        tau = W.double_shear_2d_tau(n, mach)
+        with B.Solver(B.D2Q9, (n, n, 1), tau, stream=stream) as s:
+            s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
+                          torch.from_numpy(u.astype(np.float32)).cuda())
+            e0 = s.diagnostics()[-1]
+            s.step(24)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            e1 = s.diagnostics()[-1]
+        gbs = 72.0 * n * n * steps / (ms * 1e-3) / 1e9
+        out["runs"][f"ma{mach}"] = {"tau": tau, "glups": n * n * steps / (ms * 1e-3) / 1e9,
+                                    "kernel_gbs": gbs, "roofline_frac": gbs / peak_gbs,
+                                    "ms": ms, "ke_end_over_start": e1 / e0}
+    return out
+
+
 def dipole_variant(B, N: int = 500):
     """The dipole-wall collision (walls, D2Q9, Re 2500) at N = 500 with each
     storage precision: the two enstrophy maxima against the reference values
@@ -415,6 +446,8 @@ def run_gpu(args):
     variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
                                           sync_all, main["total_ms"] / args.steps)
     variants["dipole_wall"] = dipole_variant(B)
+    variants["d2q9_shear_2048"] = shear_variant(B, torch, stream,
+                                                float(_peaks().get("hbm_gbs", 6800.0)))
 
     total_ms, kernel_ms, e2e_s = max_over_ranks(dist, [main["total_ms"], main["kernel_ms"], e2e_s],
                                                 "cuda")
