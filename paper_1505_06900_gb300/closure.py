@@ -206,3 +206,38 @@ def study(n_fine=64, mach=0.3, re=1600.0, train_seeds=range(1, 9), eval_seed=9,
               "n_fine": n_fine, "mach": mach, "re": re}
     report.update(evaluate(net, n_fine, mach, re, eval_seed, coarse_steps))
     return net, report
+
+
+def main():
+    """The recipe at a chosen size, printed as one JSON line: the training
+    statistics, the held-out phase's a priori check and the velocity errors
+    of coarse RR with and without the closure against the filtered fine run.
+
+        python -m paper_1505_06900_gb300.closure --n-fine 512 --fraction 0.02
+    """
+    import argparse
+    import json
+    import time
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-fine", type=int, default=128)
+    ap.add_argument("--fraction", type=float, default=0.25)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--coarse-steps", type=int, default=400)
+    ap.add_argument("--snapshots", type=int, nargs="+", default=[200, 400, 600, 800])
+    args = ap.parse_args()
+    t0 = time.perf_counter()
+    net, rep = study(n_fine=args.n_fine, fraction=args.fraction, steps=args.steps,
+                     coarse_steps=args.coarse_steps, snapshots=tuple(args.snapshots))
+    rep["seconds_study"] = time.perf_counter() - t0
+    rep["held_out_a_priori"] = held_out_loss(net, args.n_fine, rep["mach"], rep["re"], 9,
+                                             tuple(args.snapshots))
+    rep["fraction"] = args.fraction
+    rep["adam_steps"] = args.steps
+    net.close()
+    print(json.dumps(rep), flush=True)
+
+
+if __name__ == "__main__":
+    main()
+
