@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbrr.h"
 #include "lbrr_launch.h"
 #include "lbrr_mlp.h"
@@ -79,6 +81,13 @@ int cuda_fail(lb_ctx *c, cudaError_t e, const char *what) {
   do {                                                          \
     if (!(c)) return fail(nullptr, LB_EINVAL, "null context");  \
   } while (0)
+
+// NVTX range around an entry point (shown by nsys and other tracing tools;
+// free when no tool is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 // Make the context's device current for the duration of a call.
 struct DeviceGuard {
@@ -267,6 +276,7 @@ int lb_set_stream(lb_ctx *c, void *stream) {
 }
 
 int lb_init_fields(lb_ctx *c, const float *rho, const float *u, int init_mode) {
+  Range nvtx_range("lb_init_fields");
   LB_CHECK_CTX(c);
   if (!rho || !u) return fail(c, LB_EINVAL, "rho and u must be device pointers");
   if (init_mode != LB_INIT_EQ && init_mode != LB_INIT_EQ_NEQ_FD)
@@ -317,6 +327,7 @@ cudaGraphExec_t step_graph(lb_ctx *c, float om1) {
 }  // namespace
 
 int lb_step(lb_ctx *c, int n) {
+  Range nvtx_range("lb_step");
   LB_CHECK_CTX(c);
   if (n < 0) return fail(c, LB_EINVAL, "negative step count %d", n);
   DeviceGuard dg(c->device);
@@ -366,6 +377,7 @@ int lb_step(lb_ctx *c, int n) {
 }
 
 int lb_moments(lb_ctx *c, float *rho, float *u, float *pi1) {
+  Range nvtx_range("lb_moments");
   LB_CHECK_CTX(c);
   if (!rho && !u && !pi1) return LB_OK;
   DeviceGuard dg(c->device);
@@ -376,6 +388,7 @@ int lb_moments(lb_ctx *c, float *rho, float *u, float *pi1) {
 }
 
 int lb_diagnostics(lb_ctx *c, double *out) {
+  Range nvtx_range("lb_diagnostics");
   LB_CHECK_CTX(c);
   if (!out) return fail(c, LB_EINVAL, "null output");
   DeviceGuard dg(c->device);
@@ -383,6 +396,7 @@ int lb_diagnostics(lb_ctx *c, double *out) {
 }
 
 int lb_enstrophy(lb_ctx *c, double *out) {
+  Range nvtx_range("lb_enstrophy");
   LB_CHECK_CTX(c);
   if (!out) return fail(c, LB_EINVAL, "null output");
   DeviceGuard dg(c->device);
@@ -426,6 +440,7 @@ long long lb_state_bytes(const lb_ctx *c) {
 }
 
 int lb_get_state(lb_ctx *c, void *dst, int *parity) {
+  Range nvtx_range("lb_get_state");
   LB_CHECK_CTX(c);
   if (!dst || !parity) return fail(c, LB_EINVAL, "null argument");
   DeviceGuard dg(c->device);
@@ -445,6 +460,7 @@ int lb_get_state(lb_ctx *c, void *dst, int *parity) {
 }
 
 int lb_set_state(lb_ctx *c, const void *src, int parity) {
+  Range nvtx_range("lb_set_state");
   LB_CHECK_CTX(c);
   if (!src) return fail(c, LB_EINVAL, "null source");
   if (parity != 0 && parity != 1) return fail(c, LB_EINVAL, "parity must be 0 or 1");
@@ -460,6 +476,7 @@ int lb_set_state(lb_ctx *c, const void *src, int parity) {
 
 int lb_run_host(lb_ctx *c, const float *rho_h, const float *u_h, int init_mode, int nsteps,
                 float *rho_out_h, float *u_out_h, double *diag_h) {
+  Range nvtx_range("lb_run_host");
   LB_CHECK_CTX(c);
   if (!rho_h || !u_h) return fail(c, LB_EINVAL, "rho and u must be host pointers");
   if (nsteps < 0) return fail(c, LB_EINVAL, "negative step count");
@@ -694,6 +711,7 @@ int lb_mlp_gradients(lb_mlp *m, const void *X, const float *T, long long M, floa
 
 int lb_mlp_train_step(lb_mlp *m, const void *X, const float *T, long long M, float lr,
                       double *loss) {
+  Range nvtx_range("lb_mlp_train_step");
   return mlp_backward(m, X, T, M, nullptr, 1, lr, loss);
 }
 
@@ -756,6 +774,7 @@ int lb_closure_targets(lb_ctx *c, const lb_mlp *m, float *T) {
 }
 
 int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
+  Range nvtx_range("lb_coarsen");
   LB_CHECK_CTX(fine);
   LB_CHECK_CTX(coarse);
   if (fine->lattice != LB_D3Q27 || coarse->lattice != LB_D3Q27 || fine->storage != LB_STORE_F32 ||
