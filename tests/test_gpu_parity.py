@@ -237,3 +237,44 @@ def test_step_runs_replayed_as_graphs_equal_single_updates(lattice, shape, walls
         assert a.info()["steps"] == b.info()["steps"] == 58
         assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
 
+
+@pytest.mark.parametrize("lattice,shape", [(O.D3Q27, (1, 1, 1)), (O.D3Q19, (1, 1, 1)),
+                                           (O.D2Q9, (1, 1, 1)), (O.D3Q27, (1, 5, 4)),
+                                           (O.D3Q19, (4, 1, 3)), (O.D2Q9, (1, 7, 1))])
+def test_degenerate_grids_match_oracle(lattice, shape):
+    """One-cell and one-column periodic grids: every neighbour along a unit
+    axis is the cell itself (the wrap of the AA gather and scatter)."""
+    tau = 0.7
+    df = _random_state(lattice, shape, seed=61)
+    with _solver(lattice, shape, tau) as s:
+        s.set_populations(_cuda(df))
+        f = f64_state(lattice, df)
+        for k in range(3):
+            s.step(1)
+            f = O.step(lattice, shape, tau, f, 1)
+            err = max_rel_to_weight(lattice, s.populations().cpu().numpy(), shifted(lattice, f))
+            assert err <= ONE_STEP_TOL, (k, err)
+
+
+@pytest.mark.parametrize("lattice", [O.D2Q9, O.D3Q19, O.D3Q27])
+@pytest.mark.parametrize("storage", [B.STORE_F32, B.STORE_F16, B.STORE_BF16])
+def test_rest_and_uniform_flow_are_kept(lattice, storage):
+    """The rest state is a fixed point bit for bit (df = 0 stays 0), and a
+    uniform flow stays uniform bit for bit: every cell runs the same
+    arithmetic, whatever the AA parity and the kernel."""
+    d, _ = O.dims_of(lattice)
+    shape = (256, 4, 3) if d == 3 else (256, 6, 1)
+    with _solver(lattice, shape, 0.6, storage=storage) as s:
+        s.step(20)
+        assert not np.any(s.populations().cpu().numpy())
+        rho = np.full(shape[::-1], 1.01, np.float32)
+        u = np.zeros((d,) + shape[::-1], np.float32)
+        u[0], u[1] = 0.05, -0.02
+        s.init_fields(_cuda(rho), _cuda(u), B.INIT_EQ)
+        s.step(21)
+        df = s.populations().cpu().numpy().reshape(s.q, -1)
+        assert np.all(df == df[:, :1])
+        r, uu, _ = (t.cpu().numpy() for t in s.moments())
+        assert np.all(r == r.flat[0]) and np.all(uu[0] == uu[0].flat[0])
+        assert abs(float(uu[0].flat[0]) - 0.05) < (1e-6 if storage == B.STORE_F32 else 2e-3)
+
