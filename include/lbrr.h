@@ -265,7 +265,13 @@ LB_API int lb_coarsen(lb_ctx *fine, lb_ctx *coarse);
 /* Use the network in lb_step (NULL: plain RR). A cell whose standardised
  * prediction exceeds `bound` in magnitude, or whose corrected populations are
  * not all positive, takes the RR update instead and is counted. The network
- * must outlive its use. */
+ * must outlive its use. On grids whose rows are whole 128-cell tiles an
+ * update is two kernels: the standardised moments of every cell (BF16), then
+ * the tcgen05 network, whose epilogue performs the corrected update of each
+ * tile row's cell in place; on other grids the predictions go through device
+ * memory to a separate update kernel. If a bounded wait of the network
+ * expires (reported as LB_ETIMEOUT), part of the cells of that update were
+ * not updated: re-initialise or restore a checkpoint. */
 LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
 /* Cells that fell back to RR since the closure was first set (host out).
  * Synchronises; LB_ETIMEOUT if a bounded tensor-core wait of the closure's
