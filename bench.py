@@ -41,8 +41,8 @@ MACH, RE = 0.1, 1600.0
 # + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
 # taken on; reported as null when the sources have changed since.
 # The 512^3 launch is too large for a multi-pass capture; the value is the
-# 256^3 capture (profiles/rr_step_d3q19_d3q27_256.md, mean of the even and
-# odd launches, 212.5 B per cell) scaled by the cell count, since the traffic
+# single-pass capture of the same kernel at 256^3 (mean of the even and odd
+# launches, 212.5 B per cell) scaled by the cell count, since the traffic
 # per cell does not depend on the grid size for this streaming kernel.
 TRAFFIC = {
     "d3q27_f32_512": {"kernel_sha": "f93afdb57dff9bb0", "bytes_per_launch": 28514870272,
