@@ -278,3 +278,32 @@ def test_rest_and_uniform_flow_are_kept(lattice, storage):
         assert np.all(r == r.flat[0]) and np.all(uu[0] == uu[0].flat[0])
         assert abs(float(uu[0].flat[0]) - 0.05) < (1e-6 if storage == B.STORE_F32 else 2e-3)
 
+
+def test_side_stream_and_caller_graph_capture():
+    """A context on a side stream (graph replay included) gives the results of
+    one on the default stream, bit for bit; inside the caller's own CUDA-graph
+    capture lb_step records its updates one by one into that capture, and
+    replaying the captured graph advances the state as the direct call does."""
+    shape = (64, 12, 10)
+    rho, u = W.as_f32(*W.random_field(shape, 3, seed=71, a_rho=0.01, a_u=0.03))
+    rd, ud = _cuda(rho), _cuda(u)
+    with _solver(O.D3Q27, shape, 0.62) as ref:
+        ref.init_fields(rd, ud)
+        ref.step(40)
+        want = ref.populations().cpu().numpy()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with B.Solver(O.D3Q27, shape, 0.62, stream=side) as s:
+            s.init_fields(rd, ud)
+            s.step(24)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+                s.set_stream(side)
+                s.step(16)
+            g.replay()
+            side.synchronize()
+            assert s.info()["steps"] == 40
+            got = s.populations().cpu().numpy()
+    assert np.array_equal(got, want)
+
