@@ -415,39 +415,43 @@ def run_gpu(args):
     d2h = (rho32.nbytes + u32.nbytes) + diag_h.nbytes
     del rho_h, u_h, rho_o, u_o
 
+    # the storage, lattice and closure variants and the other workloads belong to
+    # the single-GPU line; a multi-GPU run times the headline workload only
     variants = {}
-    for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
-        r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                         DIAG_EVERY, stream, sync_all, keep_u=True)
-        variants[name] = {
-            "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
-            "bytes_per_update": r["bytes_per_update"],
-            "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
-            "speedup_vs_f32": main["total_ms"] / r["total_ms"],
-            "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
-            "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, same init",
-        }
-    # D3Q19 (Sec. 5): 19 populations per cell, the same flow and tau
-    for name, st in (("d3q19_f32", B.STORE_F32), ("d3q19_f16", B.STORE_F16)):
-        r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                         DIAG_EVERY, stream, sync_all, keep_u=True, lattice=B.D3Q19)
-        kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
-        variants[name] = {
-            "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
-            "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
-            "roofline_frac": kgbs / (float(_peaks().get("hbm_gbs", 6800.0))),
-            "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
-            "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
-            "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after "
-                           f"{args.warmup + args.steps} steps, same init (lattice + storage "
-                           f"difference)",
-        }
-    del u_f32
-    variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
-                                          sync_all, main["total_ms"] / args.steps)
-    variants["dipole_wall"] = dipole_variant(B)
-    variants["d2q9_shear_2048"] = shear_variant(B, torch, stream,
-                                                float(_peaks().get("hbm_gbs", 6800.0)))
+    if ws == 1:
+        for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
+            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                             DIAG_EVERY, stream, sync_all, keep_u=True)
+            variants[name] = {
+                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                "bytes_per_update": r["bytes_per_update"],
+                "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
+                "speedup_vs_f32": main["total_ms"] / r["total_ms"],
+                "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
+                "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, "
+                                "same init",
+            }
+        # D3Q19 (Sec. 5): 19 populations per cell, the same flow and tau
+        for name, st in (("d3q19_f32", B.STORE_F32), ("d3q19_f16", B.STORE_F16)):
+            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                             DIAG_EVERY, stream, sync_all, keep_u=True, lattice=B.D3Q19)
+            kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
+            variants[name] = {
+                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
+                "roofline_frac": kgbs / (float(_peaks().get("hbm_gbs", 6800.0))),
+                "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
+                "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
+                "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after "
+                               f"{args.warmup + args.steps} steps, same init (lattice + storage "
+                               f"difference)",
+            }
+        del u_f32
+        variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
+                                              sync_all, main["total_ms"] / args.steps)
+        variants["dipole_wall"] = dipole_variant(B)
+        variants["d2q9_shear_2048"] = shear_variant(B, torch, stream,
+                                                    float(_peaks().get("hbm_gbs", 6800.0)))
 
     total_ms, kernel_ms, e2e_s = max_over_ranks(dist, [main["total_ms"], main["kernel_ms"], e2e_s],
                                                 "cuda")
@@ -466,7 +470,8 @@ def run_gpu(args):
     tr = TRAFFIC.get(f"d3q27_f32_{n}")
     traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == sha else None
 
-    cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample)
+    # the CPU oracle is timed beside the single-GPU run only
+    cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample) if ws == 1 else None
     clocks = sampler.summary()
     value = job_glups(ws, cells, args.steps, total_ms)
     line = {
@@ -490,7 +495,8 @@ def run_gpu(args):
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "scope": "lb_run_host: pinned upload of rho,u, init, K updates, download of "
                          "rho,u and diagnostics"},
-        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+                         if cpu else None),
         "gpu_launches": main["launches"],
         "clocks": clocks,
         "kernel_sha": sha,
