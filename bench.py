@@ -471,7 +471,9 @@ def run_gpu(args):
     traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == sha else None
 
     # the CPU oracle is timed beside the single-GPU run only
-    cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample) if ws == 1 else None
+    cpu = None
+    if ws == 1:
+        cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample)
     clocks = sampler.summary()
     value = job_glups(ws, cells, args.steps, total_ms)
     line = {
