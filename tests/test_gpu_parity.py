@@ -111,6 +111,24 @@ def test_taylor_green_2d_1000_steps():
     assert rel_l2(r_g, r_o) <= 1e-6
 
 
+@pytest.mark.parametrize("mach", [0.1, 0.3, 0.5])
+def test_double_shear_layer_128_1000_steps(mach):
+    """The 128^2 copy of the D2Q9 double shear layer (Re 1000 on L = 128), 1000
+    updates against the oracle, at each Mach number of the 2048^2 workload."""
+    n = 128
+    tau = W.double_shear_2d_tau(n, mach)
+    rho, u = W.as_f32(*W.double_shear_2d(n, mach))
+    shape = (n, n, 1)
+    with _solver(O.D2Q9, shape, tau) as s:
+        s.init_fields(_cuda(rho), _cuda(u))
+        s.step(1000)
+        r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
+    f = O.step(O.D2Q9, shape, tau, O.init(O.D2Q9, shape, tau, rho, u), 1000)
+    r_o, u_o, _ = O.fields(O.D2Q9, shape, f)
+    assert rel_l2(u_g, u_o) <= 1e-5
+    assert rel_l2(r_g, r_o) <= 1e-6
+
+
 @pytest.mark.parametrize("lattice", [O.D3Q27, O.D3Q19])
 def test_taylor_green_3d_1000_steps(lattice):
     """3-D Taylor-Green vortex (Ma = 0.1, Re = 1600) on 24^3, 1000 updates."""
