@@ -210,6 +210,7 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
     s = B.Solver(lattice, (n, n, n), tau, storage=storage, stream=stream)
     try:
         s.init_fields(rho_d, u_d)
+        diag0 = s.diagnostics()
         if closure is not None:
             s.set_closure(closure)
         s.step(warmup)
@@ -243,7 +244,8 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         diag = s.diagnostics()
         out = {"total_ms": total_ms, "kernel_ms": statistics.mean(kern_ms),
                "kernel_ms_median": statistics.median(kern_ms), "launches": launches,
-               "diag": diag.tolist(), "bytes_per_update": s.info()["bytes_per_update"]}
+               "diag": diag.tolist(), "diag0": diag0.tolist(),
+               "bytes_per_update": s.info()["bytes_per_update"]}
         if keep_u:
             out["u"] = s.moments()[1]
         if closure is not None:
@@ -251,6 +253,12 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         return out
     finally:
         s.close()
+
+
+def ke_decay_vs(r, ref) -> float:
+    """Kinetic energy lost over the run (start minus end) relative to that of
+    the reference run, minus one."""
+    return (r["diag0"][-1] - r["diag"][-1]) / (ref["diag0"][-1] - ref["diag"][-1]) - 1.0
 
 
 def rel_l2(torch, a, b) -> float:
@@ -428,6 +436,7 @@ def run_gpu(args):
                 "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
                 "speedup_vs_f32": main["total_ms"] / r["total_ms"],
                 "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
+                "ke_decay_vs_f32": ke_decay_vs(r, main),
                 "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, "
                                 "same init",
             }
@@ -442,11 +451,16 @@ def run_gpu(args):
                 "roofline_frac": kgbs / (float(_peaks().get("hbm_gbs", 6800.0))),
                 "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
                 "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
+                "ke_decay_vs_d3q27_f32": ke_decay_vs(r, main),
                 "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after "
                                f"{args.warmup + args.steps} steps, same init (lattice + storage "
                                f"difference)",
             }
         del u_f32
+        # context for the decay ratios: the share of its kinetic energy the FP32 run loses
+        # over these updates (the Taylor-Green vortex at 512^3 decays slowly)
+        ke0, ke1 = main["diag0"][-1], main["diag"][-1]
+        variants["ke_loss_fraction_f32"] = (ke0 - ke1) / ke0
         variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
                                               sync_all, main["total_ms"] / args.steps)
         variants["dipole_wall"] = dipole_variant(B)

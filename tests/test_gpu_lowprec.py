@@ -133,15 +133,18 @@ _ORACLE_3D = {}
 
 
 def _oracle_tgv_3d(lattice):
-    """rho, u of the FP64 oracle after 1000 updates (computed once per lattice)."""
+    """rho, u of the FP64 oracle after 1000 updates and its kinetic energy at
+    the start and the end (computed once per lattice)."""
     if lattice not in _ORACLE_3D:
         n = N_3D
         tau = W.taylor_green_3d_tau(n, 0.1)
         rho, u = W.as_f32(*W.taylor_green_3d(n, 0.1))
         shape = (n, n, n)
-        f = O.step(lattice, shape, tau, O.init(lattice, shape, tau, rho, u), 1000)
+        f0 = O.init(lattice, shape, tau, rho, u)
+        f = O.step(lattice, shape, tau, f0, 1000)
         r_o, u_o, _ = O.fields(lattice, shape, f)
-        _ORACLE_3D[lattice] = (r_o, u_o)
+        ke = (O.diagnostics(lattice, shape, f0)[-1], O.diagnostics(lattice, shape, f)[-1])
+        _ORACLE_3D[lattice] = (r_o, u_o, ke)
     return _ORACLE_3D[lattice]
 
 
@@ -154,10 +157,15 @@ def test_error_budget_3d_1000_updates(lattice, storage):
     with B.Solver(lattice, (n, n, n), tau, storage=storage) as s:
         s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
                       torch.from_numpy(u.astype(np.float32)).cuda())
+        ke0 = s.diagnostics()[-1]
         s.step(1000)
+        ke1 = s.diagnostics()[-1]
         r_g, u_g, _ = (t.cpu().numpy() for t in s.moments())
-    r_o, u_o = _oracle_tgv_3d(lattice)
+    r_o, u_o, ke_o = _oracle_tgv_3d(lattice)
     eu, er = rel_l2(u_g, u_o), rel_l2(r_g, r_o)
-    print(f"lattice {lattice} storage {storage}: u {eu:.3e} rho {er:.3e}")
+    # kinetic energy lost over the 1000 updates against the oracle's loss
+    decay = (ke0 - ke1) / (ke_o[0] - ke_o[1]) - 1.0
+    print(f"lattice {lattice} storage {storage}: u {eu:.3e} rho {er:.3e} "
+          f"energy decay {decay:+.2e}")
     assert eu <= BUDGET_3D[storage]["u"]
     assert er <= BUDGET_3D[storage]["rho"]
