@@ -36,6 +36,8 @@ METRIC = "GLUPS & %HBM roofline, D3Q27 RR: FP32 vs FP16-store vs learned at fixe
 UNIT = "GLUPS"
 DIAG_EVERY = 50
 MACH, RE = 0.1, 1600.0
+U_ERROR_UPDATES = 1000   # updates after which the 16-bit forms' u error is taken
+RATED_HBM_GBS = 7900.0   # nominal GB300 HBM3e bandwidth, beside the measured copy peak
 
 # DRAM traffic of one step-kernel launch from an ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
@@ -67,22 +69,26 @@ def log(*a):
 
 # ------------------------------------------------------------------ clocks --
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clock and throttle reasons, every 50 ms, over the
+    whole GPU arm; each sample carries its host time, so a summary can be taken
+    over the timed region alone (mark() brackets it) and over the arm."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.lines = []
+        self.samples = []  # (host time, line)
+        self.regions = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -92,7 +98,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.samples.append((time.monotonic(), line.strip()))
+
+    def mark(self, t0: float, t1: float):
+        """Record a timed region [t0, t1] (host monotonic seconds)."""
+        self.regions.append((t0, t1))
 
     def __exit__(self, *exc):
         if self.proc:
@@ -102,10 +112,11 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
+    @staticmethod
+    def _summarise(lines):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -122,6 +133,17 @@ class ClockSampler:
         loaded = [s for s in sm if smax and s > 0.5 * smax] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+    def summary(self):
+        """Summary over the marked timed regions (samples taken while one was
+        running, widened by half a period at each end), plus the whole arm."""
+        half = 0.5 * self.PERIOD_MS / 1e3
+        inside = [ln for t, ln in self.samples
+                  if any(a - half <= t <= b + half for a, b in self.regions)]
+        out = self._summarise(inside)
+        out["period_ms"] = self.PERIOD_MS
+        out["arm"] = self._summarise([ln for _, ln in self.samples])
+        return out
 
 
 # --------------------------------------------------------------- distributed --
@@ -203,9 +225,11 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm --
 def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_every, stream,
-                 sync_all, sampler=None, keep_u=False, closure=None, lattice=None):
-    """Warm up, then time `steps` updates; returns timing and per-launch data
-    (and the final velocity field with keep_u). Lattice D3Q27 unless given."""
+                 sync_all, sampler=None, u_at=None, closure=None, lattice=None):
+    """Warm up, then time `steps` updates with the diagnostics reduction every
+    `diag_every` updates inside the timed region; returns timing and per-launch
+    data. With u_at, the run then continues (untimed) to u_at updates in all
+    and returns the velocity field there. Lattice D3Q27 unless given."""
     lattice = B.D3Q27 if lattice is None else lattice
     s = B.Solver(lattice, (n, n, n), tau, storage=storage, stream=stream)
     try:
@@ -224,30 +248,35 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         sync_all()
         torch.cuda.synchronize()
         launches = 0
-        ctx = sampler if sampler is not None else _Null()
-        with ctx:
-            with torch.cuda.stream(stream):
-                t_start.record(stream)
-                for k in range(steps):
-                    ev[k][0].record(stream)
-                    s.step(1)
-                    ev[k][1].record(stream)
-                    launches += 1
-                    if (k + 1) % diag_every == 0:
-                        s.diagnostics()
-                        launches += 2
-                t_end.record(stream)
-            torch.cuda.synchronize()
+        diag_calls = 0
+        h0 = time.monotonic()
+        with torch.cuda.stream(stream):
+            t_start.record(stream)
+            for k in range(steps):
+                ev[k][0].record(stream)
+                s.step(1)
+                ev[k][1].record(stream)
+                launches += 1
+                if (k + 1) % diag_every == 0:
+                    s.diagnostics()
+                    launches += 2
+                    diag_calls += 1
+            t_end.record(stream)
+        torch.cuda.synchronize()
+        if sampler is not None:
+            sampler.mark(h0, time.monotonic())
         sync_all()
         total_ms = t_start.elapsed_time(t_end)
         kern_ms = [a.elapsed_time(b) for a, b in ev]
         diag = s.diagnostics()
         out = {"total_ms": total_ms, "kernel_ms": statistics.mean(kern_ms),
                "kernel_ms_median": statistics.median(kern_ms), "launches": launches,
-               "diag": diag.tolist(), "diag0": diag0.tolist(),
+               "diag_calls": diag_calls, "diag": diag.tolist(), "diag0": diag0.tolist(),
                "bytes_per_update": s.info()["bytes_per_update"]}
-        if keep_u:
+        if u_at is not None:
+            s.step(max(0, u_at - warmup - steps))
             out["u"] = s.moments()[1]
+            out["diag_u_at"] = s.diagnostics().tolist()
         if closure is not None:
             out["fallbacks"] = s.closure_fallbacks()
         return out
@@ -255,17 +284,26 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         s.close()
 
 
-def ke_decay_vs(r, ref) -> float:
+def ke_decay_vs(r, ref, key="diag") -> float:
     """Kinetic energy lost over the run (start minus end) relative to that of
     the reference run, minus one."""
-    return (r["diag0"][-1] - r["diag"][-1]) / (ref["diag0"][-1] - ref["diag"][-1]) - 1.0
+    return (r["diag0"][-1] - r[key][-1]) / (ref["diag0"][-1] - ref[key][-1]) - 1.0
 
 
 def rel_l2(torch, a, b) -> float:
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
-def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms_per_step):
+# Algorithmic cost of one closure update per coarse cell: the populations read
+# and written (216 B) plus a BF16 moment field of 10 channels written once and
+# read once for the 3^3 gather (40 B); the network's padded BF16 products
+# 2 (288 x 64 + 64 x 64 + 64 x 32) flops.
+CLOSURE_BYTES_PER_CELL = 256
+CLOSURE_FLOP_PER_CELL = 2 * (288 * 64 + 64 * 64 + 64 * 32)
+
+
+def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms_per_step,
+                    sampler=None):
     """Train the closure on the filtered 128^3 study (seconds), then time the
     closure step on an n_coarse^3 grid (one coarse step stands for two fine
     steps of the 2 n_coarse grid) next to plain RR on the same coarse grid."""
@@ -279,30 +317,35 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
     rho, u = W.taylor_green_3d(n_coarse, MACH)
     rho_d = torch.from_numpy(rho.astype(np.float32)).cuda()
     u_d = torch.from_numpy(u.astype(np.float32)).cuda()
+    diag_every = min(DIAG_EVERY, steps)
     ml = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
-                      DIAG_EVERY, stream, sync_all, closure=net)
+                      diag_every, stream, sync_all, sampler, closure=net)
     rr = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
-                      DIAG_EVERY, stream, sync_all)
+                      diag_every, stream, sync_all, sampler)
     cells = n_coarse ** 3
     ms_ml = ml["total_ms"] / steps
     ms_rr = rr["total_ms"] / steps
     net.close()
+    peaks = _peaks()
+    gbs = CLOSURE_BYTES_PER_CELL * cells / (ms_ml * 1e-3) / 1e9
+    tfs = CLOSURE_FLOP_PER_CELL * cells / (ms_ml * 1e-3) / 1e12
     return {
         "value": cells * steps / (ml["total_ms"] * 1e-3) / 1e9, "unit": "GLUPS (coarse cells)",
         "grid": [n_coarse] * 3, "ms_per_coarse_step": ms_ml,
         "kernels_per_step": 2,
         "kernels": "feature source (moments, BF16, padded), TMA-fed tcgen05 network fused with "
                    "the corrected RR update",
+        "roofline_frac": gbs / float(peaks.get("hbm_gbs", 6800.0)),
+        "tensor_frac": tfs / float(peaks.get("bf16_tflops_sustained", 1700.0)),
         "speedup_vs_fine_f32_equal_time": 2.0 * fine_ms_per_step / ms_ml,
         "coarse_rr": {"ms_per_coarse_step": ms_rr,
                       "speedup_vs_fine_f32_equal_time": 2.0 * fine_ms_per_step / ms_rr},
         "fallback_cell_updates": ml["fallbacks"],
-        "u_error_vs_filtered_fine": {
-            "closure": rep["err_closure"], "coarse_rr": rep["err_rr"],
-            "study": f"D3Q27 Taylor-Green Ma {rep['mach']} Re {rep['re']:g}, fine "
-                     f"{rep['n_fine']}^3 -> coarse {rep['n_fine'] // 2}^3, held-out phase, "
-                     f"{rep['coarse_steps']} coarse steps",
-        },
+        "u_error_vs_filtered_fine": rep["err_closure"],
+        "coarse_rr_u_error_vs_filtered_fine": rep["err_rr"],
+        "error_sizes": f"D3Q27 Taylor-Green Ma {rep['mach']} Re {rep['re']:g}, fine "
+                       f"{rep['n_fine']}^3 -> coarse {rep['n_fine'] // 2}^3, held-out phase, "
+                       f"{rep['coarse_steps']} coarse steps",
         "training": {"samples": rep["samples"], "loss_first": rep["loss_first"],
                      "loss_last": rep["loss_last"], "seconds": train_s},
     }
@@ -400,72 +443,85 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     cells = n ** 3
 
+    # the diagnostics reduction runs inside every timed region, at least once
+    diag_every = min(DIAG_EVERY, args.steps)
+    # the 16-bit and D3Q19 forms are compared with the FP32 run after the same
+    # number of updates, at least 1000 whatever --steps is
+    n_cmp = max(U_ERROR_UPDATES, args.warmup + args.steps)
+    single = ws == 1
     sampler = ClockSampler(local)
-    main = time_variant(B, torch, n, B.STORE_F32, args.steps, args.warmup, tau, rho_d, u_d,
-                        DIAG_EVERY, stream, sync_all, sampler, keep_u=True)
-    u_f32 = main.pop("u")
-    # end to end through host buffers (pinned), one lb_run_host call of K steps,
-    # right after the device-timed run it is compared with
-    rho_h = torch.from_numpy(rho32).pin_memory()
-    u_h = torch.from_numpy(u32).pin_memory()
-    rho_o = torch.empty_like(rho_h).pin_memory()
-    u_o = torch.empty_like(u_h).pin_memory()
-    diag_h = np.zeros(5)
-    with B.Solver(B.D3Q27, (n, n, n), tau, stream=stream) as s:
-        s.run_host(rho_h, u_h, 2, rho_out=rho_o, u_out=u_o, diag_out=diag_h)  # warm-up
-        sync_all()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s.run_host(rho_h, u_h, args.steps, rho_out=rho_o, u_out=u_o, diag_out=diag_h)
-        e2e_s = time.perf_counter() - t0
-        sync_all()
-    h2d = (rho32.nbytes + u32.nbytes)
-    d2h = (rho32.nbytes + u32.nbytes) + diag_h.nbytes
-    del rho_h, u_h, rho_o, u_o
+    with sampler:
+        main = time_variant(B, torch, n, B.STORE_F32, args.steps, args.warmup, tau, rho_d, u_d,
+                            diag_every, stream, sync_all, sampler,
+                            u_at=n_cmp if single else None)
+        u_f32 = main.pop("u", None)
+        # end to end through host buffers (pinned), one lb_run_host call of K steps,
+        # right after the device-timed run it is compared with
+        rho_h = torch.from_numpy(rho32).pin_memory()
+        u_h = torch.from_numpy(u32).pin_memory()
+        rho_o = torch.empty_like(rho_h).pin_memory()
+        u_o = torch.empty_like(u_h).pin_memory()
+        diag_h = np.zeros(5)
+        with B.Solver(B.D3Q27, (n, n, n), tau, stream=stream) as s:
+            s.run_host(rho_h, u_h, 2, rho_out=rho_o, u_out=u_o, diag_out=diag_h)  # warm-up
+            sync_all()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.run_host(rho_h, u_h, args.steps, rho_out=rho_o, u_out=u_o, diag_out=diag_h)
+            e2e_s = time.perf_counter() - t0
+            sync_all()
+        h2d = (rho32.nbytes + u32.nbytes)
+        d2h = (rho32.nbytes + u32.nbytes) + diag_h.nbytes
+        del rho_h, u_h, rho_o, u_o
 
-    # the storage, lattice and closure variants and the other workloads belong to
-    # the single-GPU line; a multi-GPU run times the headline workload only
-    variants = {}
-    if ws == 1:
-        for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
-            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                             DIAG_EVERY, stream, sync_all, keep_u=True)
-            variants[name] = {
-                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
-                "bytes_per_update": r["bytes_per_update"],
-                "kernel_gbs": r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9,
-                "speedup_vs_f32": main["total_ms"] / r["total_ms"],
-                "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
-                "ke_decay_vs_f32": ke_decay_vs(r, main),
-                "u_error_note": f"relative L2 of u after {args.warmup + args.steps} steps, "
-                                "same init",
-            }
-        # D3Q19 (Sec. 5): 19 populations per cell, the same flow and tau
-        for name, st in (("d3q19_f32", B.STORE_F32), ("d3q19_f16", B.STORE_F16)):
-            r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
-                             DIAG_EVERY, stream, sync_all, keep_u=True, lattice=B.D3Q19)
-            kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
-            variants[name] = {
-                "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
-                "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
-                "roofline_frac": kgbs / (float(_peaks().get("hbm_gbs", 6800.0))),
-                "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
-                "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
-                "ke_decay_vs_d3q27_f32": ke_decay_vs(r, main),
-                "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after "
-                               f"{args.warmup + args.steps} steps, same init (lattice + storage "
-                               f"difference)",
-            }
-        del u_f32
-        # context for the decay ratios: the share of its kinetic energy the FP32 run loses
-        # over these updates (the Taylor-Green vortex at 512^3 decays slowly)
-        ke0, ke1 = main["diag0"][-1], main["diag"][-1]
-        variants["ke_loss_fraction_f32"] = (ke0 - ke1) / ke0
-        variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup, stream,
-                                              sync_all, main["total_ms"] / args.steps)
-        variants["dipole_wall"] = dipole_variant(B)
-        variants["d2q9_shear_2048"] = shear_variant(B, torch, stream,
-                                                    float(_peaks().get("hbm_gbs", 6800.0)))
+        # the storage, lattice and closure variants and the other workloads belong to
+        # the single-GPU line; a multi-GPU run times the headline workload only
+        variants = {}
+        if single:
+            peak_gbs = float(_peaks().get("hbm_gbs", 6800.0))
+            for name, st in (("f16", B.STORE_F16), ("bf16", B.STORE_BF16)):
+                r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                                 diag_every, stream, sync_all, sampler, u_at=n_cmp)
+                kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
+                variants[name] = {
+                    "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                    "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
+                    "roofline_frac": kgbs / peak_gbs,
+                    "roofline_frac_rated": kgbs / RATED_HBM_GBS,
+                    "speedup_vs_f32": main["total_ms"] / r["total_ms"],
+                    "u_error_vs_f32": rel_l2(torch, r.pop("u"), u_f32),
+                    "u_error_updates": n_cmp,
+                    "ke_decay_vs_f32": ke_decay_vs(r, main, "diag_u_at"),
+                    "u_error_note": f"relative L2 of u against the FP32 store after {n_cmp} "
+                                    "updates from the same initial state",
+                }
+            # D3Q19 (Sec. 5): 19 populations per cell, the same flow and tau
+            for name, st in (("d3q19_f32", B.STORE_F32), ("d3q19_f16", B.STORE_F16)):
+                r = time_variant(B, torch, n, st, args.steps, args.warmup, tau, rho_d, u_d,
+                                 diag_every, stream, sync_all, sampler, u_at=n_cmp,
+                                 lattice=B.D3Q19)
+                kgbs = r["bytes_per_update"] * cells / (r["kernel_ms"] * 1e-3) / 1e9
+                variants[name] = {
+                    "value": cells * args.steps / (r["total_ms"] * 1e-3) / 1e9, "unit": UNIT,
+                    "bytes_per_update": r["bytes_per_update"], "kernel_gbs": kgbs,
+                    "roofline_frac": kgbs / peak_gbs,
+                    "speedup_vs_d3q27_f32": main["total_ms"] / r["total_ms"],
+                    "u_diff_vs_d3q27_f32": rel_l2(torch, r.pop("u"), u_f32),
+                    "u_diff_updates": n_cmp,
+                    "ke_decay_vs_d3q27_f32": ke_decay_vs(r, main, "diag_u_at"),
+                    "u_diff_note": f"relative L2 of u against the D3Q27 FP32 run after {n_cmp} "
+                                   "updates, same init (lattice + storage difference)",
+                }
+            del u_f32
+            # context for the decay ratios: the share of its kinetic energy the FP32 run
+            # loses over the compared updates (the 512^3 Taylor-Green vortex decays slowly)
+            ke0, ke1 = main["diag0"][-1], main["diag_u_at"][-1]
+            variants["ke_loss_fraction_f32"] = (ke0 - ke1) / ke0
+            variants["learned"] = learned_variant(B, torch, n // 2, args.steps, args.warmup,
+                                                  stream, sync_all, main["total_ms"] / args.steps,
+                                                  sampler)
+            variants["dipole_wall"] = dipole_variant(B)
+            variants["d2q9_shear_2048"] = shear_variant(B, torch, stream, peak_gbs)
 
     total_ms, kernel_ms, e2e_s = max_over_ranks(dist, [main["total_ms"], main["kernel_ms"], e2e_s],
                                                 "cuda")
@@ -484,10 +540,15 @@ def run_gpu(args):
     tr = TRAFFIC.get(f"d3q27_f32_{n}")
     traffic = tr["bytes_per_launch"] if tr and tr.get("kernel_sha") == sha else None
 
-    # the CPU oracle is timed beside the single-GPU run only
+    # the CPU oracle is timed beside the single-GPU run only: on all host cores
+    # and on one core, on the same sample grid
     cpu = None
-    if ws == 1:
+    if single:
         cpu = oracle_sample(steps=args.cpu_steps, warmup=0, n_sample=args.cpu_sample)
+        one = oracle_sample(steps=args.cpu_steps_single, warmup=0, n_sample=args.cpu_sample,
+                            threads=1)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
     clocks = sampler.summary()
     value = job_glups(ws, cells, args.steps, total_ms)
     line = {
@@ -498,30 +559,49 @@ def run_gpu(args):
             "workload": f"D3Q27 recursive-regularized BGK, FP32 AA store, periodic {n}^3 "
                         f"Taylor-Green vortex Ma={MACH} Re={RE:g}",
             "lattice": "D3Q27", "grid": [n, n, n], "storage": "f32", "tau": tau,
-            "diag_every": DIAG_EVERY, "bytes_per_update": bpu,
+            "diag_every": diag_every, "diag_calls_timed": main["diag_calls"],
+            "bytes_per_update": bpu,
             "l2": f"inputs larger than L2 ({bpu // 2 * cells / 1e9:.1f} GB store)",
             "parallelism": "replicas" if ws > 1 else "single",
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "rr_step_kernel<27,f32,RR>", "peak_source": peak_src,
+                     "frac_rated": achieved / RATED_HBM_GBS, "peak_rated": RATED_HBM_GBS,
+                     "peak_rated_source": "nominal GB300 HBM3e bandwidth",
                      "kernel_ms": kernel_ms, "algorithmic_bytes_per_launch": bpu * cells},
         "variants": variants,
         "e2e": {"value": job_glups(ws, cells, args.steps, e2e_s * 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                 "scope": "lb_run_host: pinned upload of rho,u, init, K updates, download of "
                          "rho,u and diagnostics"},
-        "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
-                         if cpu else None),
+        "cpu_baseline": cpu,
         "gpu_launches": main["launches"],
         "clocks": clocks,
         "kernel_sha": sha,
         "diagnostics_end": main["diag"],
     }
+    # the three forms of the metric, where the driver's parser sees them
+    for name in ("f16", "bf16", "learned"):
+        if name in variants:
+            line[name] = summary_of(name, variants[name])
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def summary_of(name, v):
+    """The compact record of one form of the metric (FP16 / BF16 store, learned
+    closure): its rate, its velocity error and its roofline fraction."""
+    if name == "learned":
+        return {k: v.get(k) for k in ("value", "unit", "u_error_vs_filtered_fine",
+                                      "coarse_rr_u_error_vs_filtered_fine",
+                                      "speedup_vs_fine_f32_equal_time", "roofline_frac",
+                                      "tensor_frac", "ms_per_coarse_step", "error_sizes")}
+    return {k: v[k] for k in ("value", "unit", "u_error_vs_f32", "u_error_updates",
+                              "roofline_frac", "roofline_frac_rated", "speedup_vs_f32",
+                              "bytes_per_update")}
 
 
 def main():
@@ -532,6 +612,7 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--cpu-steps", type=int, default=50)
+    ap.add_argument("--cpu-steps-single", type=int, default=4)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     args = ap.parse_args()
     if args.warmup < 3:

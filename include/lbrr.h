@@ -305,16 +305,18 @@ LB_API int lb_wait_selftest(int iterations);
  * The paper has no counterpart; this is a service of the library.
  *
  * store: device pointer to a raw population store of the given lattice, size,
- * storage and AA parity, laid out as lb_get_state writes it. out: host memory,
+ * storage and AA parity, laid out as lb_get_state writes it; it must be
+ * device (or managed) memory of the current device, anything else (a host
+ * pointer, another GPU's memory) is rejected with LB_EINVAL. out: host memory,
  * 2 + D doubles (mass, momentum, kinetic energy) as in lb_diagnostics.
  * stream: cudaStream_t to order the work on (NULL: legacy default stream); the
  * call synchronises it. The reduction's partial sums live in a fixed device
  * array inside the library (1.25 MiB per GPU, held until the process exits),
  * so grids above LB_STATIC_MAX_CELLS cells are rejected with LB_EINVAL. All
  * calls on a device share that array: calls that overlap on the GPU race and
- * must be serialised by the caller. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make it before any stream
- * capture. Errors: LB_EINVAL (bad argument or grid too large), LB_ECUDA,
+ * must be serialised by the caller. The first call on a device (and in each
+ * new CUDA context of it) looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture. Errors: LB_EINVAL (bad argument or grid too large), LB_ECUDA,
  * LB_EDIVERGED (out filled, a value is not finite); lb_last_error(NULL) has
  * the text. */
 LB_API int lb_diagnostics_static(int lattice, int nx, int ny, int nz, int storage, int parity,

@@ -60,3 +60,38 @@ def max_growth(lattice: int, u, tau: float, variant: int = RR, nk: int = 97,
             if g > best:
                 best, arg = g, (kx, ky)
     return best, arg
+
+
+def growth_map(lattice: int, u, tau: float, variant: int = RR, nk: int = 97,
+               rho: float = 1.0) -> np.ndarray:
+    """max_j ln|lambda_j| on the uniform nk x nk grid of wave vectors in
+    [-pi, pi)^2 (the map of the paper's dissipation figures), shape [nk, nk]."""
+    if lattice != D2Q9:
+        raise ValueError("the k-map scan is written for D2Q9")
+    J = jacobian(lattice, rho, u, tau, variant)
+    c, _ = lattice_tables(lattice)
+    ks = np.linspace(-np.pi, np.pi, nk, endpoint=False)
+    kx, ky = np.meshgrid(ks, ks, indexing="ij")
+    phase = kx[..., None] * c[:, 0] + ky[..., None] * c[:, 1]
+    M = np.exp(-1j * phase)[..., :, None] * J
+    lam = np.linalg.eigvals(M.reshape(-1, J.shape[0], J.shape[0]))
+    return np.log(np.abs(lam)).max(axis=-1).reshape(nk, nk)
+
+
+def onset_velocity(tau: float, nk: int, lo: float = 0.2, hi: float = 0.26,
+                   tol: float = 5e-4, threshold: float = 1e-10, variant: int = RR) -> float:
+    """Smallest u_x (u_y = 0) at which some wave vector of the nk x nk map has a
+    growing mode (max growth rate above `threshold`, which lies above the
+    round-off of the numerical Jacobian), by bisection between a stable `lo`
+    and an unstable `hi`; returns the upper end of the final bracket."""
+    def unstable(ux):
+        return growth_map(D2Q9, (ux, 0.0), tau, variant, nk).max() > threshold
+    if unstable(lo) or not unstable(hi):
+        raise ValueError("the bracket does not contain the onset")
+    while hi - lo > tol:
+        mid = 0.5 * (lo + hi)
+        if unstable(mid):
+            hi = mid
+        else:
+            lo = mid
+    return hi

@@ -23,7 +23,8 @@ struct lb_ctx {
   int device = 0;
   size_t elem = 4;         // bytes per stored population
   void *f = nullptr;       // population store, q * n elements
-  double *partials = nullptr;  // reduction scratch, kRedBlocks * kRedValues doubles
+  int red_blocks = 0;          // partial-sum blocks: kRedBlocksPerSm x the device's SMs
+  double *partials = nullptr;  // reduction scratch, red_blocks * kRedValues doubles
   double *dout = nullptr;      // reduction result, kRedValues doubles
   int *status = nullptr;       // [0] set to 1 by the 16-bit row kernel if a bounded wait
                                // expired (cleared when reported), [1] its main-loop wait limit
@@ -144,8 +145,8 @@ int ensure_fields(lb_ctx *c) {
 
 // Deterministic FP64 diagnostics into host out[2 + d].
 int diagnostics(lb_ctx *c, double *out) {
-  cudaError_t e = lbrr::launch_diagnostics(c->q, c->storage, c->f, c->g, c->parity, c->partials,
-                                           c->dout, c->stream);
+  cudaError_t e = lbrr::launch_diagnostics(c->q, c->storage, c->f, c->g, c->parity,
+                                           c->red_blocks, c->partials, c->dout, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "diagnostics launch");
   double h[lbrr::kRedValues];
   int st = 0;
@@ -229,10 +230,17 @@ int lb_create_ex(lb_ctx **out, const lb_options *opt) {
     delete c;
     return fail(nullptr, LB_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
   }
+  int sms = 0;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess || sms < 1) {
+    delete c;
+    return fail(nullptr, LB_ECUDA, "cannot query the SM count: %s", cudaGetErrorString(e));
+  }
+  c->red_blocks = lbrr::kRedBlocksPerSm * sms;
   const size_t bytes = c->elem * (size_t)c->q * (size_t)n;
   e = cudaMalloc(&c->f, bytes);
   if (e == cudaSuccess)
-    e = cudaMalloc(&c->partials, sizeof(double) * lbrr::kRedBlocks * lbrr::kRedValues);
+    e = cudaMalloc(&c->partials, sizeof(double) * (size_t)c->red_blocks * lbrr::kRedValues);
   if (e == cudaSuccess) e = cudaMalloc(&c->dout, sizeof(double) * lbrr::kRedValues);
   if (e == cudaSuccess) e = cudaMalloc(&c->status, 2 * sizeof(int));
   if (e != cudaSuccess) {
@@ -405,7 +413,8 @@ int lb_enstrophy(lb_ctx *c, double *out) {
   float *u = c->fields + c->g.n;
   cudaError_t e = lbrr::launch_moments(c->q, c->storage, c->f, c->g, c->parity, nullptr, u,
                                        nullptr, c->stream);
-  if (e == cudaSuccess) e = lbrr::launch_enstrophy(c->d, u, c->g, c->partials, c->dout, c->stream);
+  if (e == cudaSuccess) e = lbrr::launch_enstrophy(c->d, u, c->g, c->red_blocks, c->partials,
+                                                    c->dout, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, c->dout, sizeof(double), cudaMemcpyDeviceToHost,
                                             c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -302,9 +302,9 @@ __global__ void __launch_bounds__(kRedThreads)
 // --------------------------------------------------------------- launchers --
 static dim3 cells_grid(long long n) { return dim3((unsigned)((n + kAuxThreads - 1) / kAuxThreads)); }
 
-static int red_blocks(long long n) {
+static int red_blocks(long long n, int max_blocks) {
   long long b = (n + kRedThreads - 1) / kRedThreads;
-  return (int)(b < kRedBlocks ? b : kRedBlocks);
+  return (int)(b < max_blocks ? b : max_blocks);
 }
 
 // Calls fn(integral_constant<Q>, integral_constant<S>) for the runtime
@@ -380,8 +380,8 @@ cudaError_t launch_moments(int q, int storage, const void *f, const Grid &g, int
 }
 
 cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g, int parity,
-                               double *partials, double *out, cudaStream_t st) {
-  const int nb = red_blocks(g.n);
+                               int max_blocks, double *partials, double *out, cudaStream_t st) {
+  const int nb = red_blocks(g.n, max_blocks);
   dispatch_qs(q, storage, [&](auto qc, auto sc) {
     constexpr int Q_ = decltype(qc)::value;
     constexpr int S_ = decltype(sc)::value;
@@ -419,9 +419,9 @@ cudaError_t launch_diagnostics_blocks(int q, int storage, const void *f, const G
   return cudaGetLastError();
 }
 
-cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
-                             cudaStream_t st) {
-  const int nb = red_blocks(g.n);
+cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, int max_blocks,
+                             double *partials, double *out, cudaStream_t st) {
+  const int nb = red_blocks(g.n, max_blocks);
   if (d == 2)
     enstrophy_partial_kernel<2><<<nb, kRedThreads, 0, st>>>(u, g, partials);
   else

@@ -7,8 +7,9 @@
 
 namespace lbrr {
 
-// Number of per-block partial sums of the deterministic reductions.
-constexpr int kRedBlocks = 1216;   // 152 SMs x 8
+// Partial-sum blocks of the deterministic reductions per SM of the device
+// (a context sizes its scratch as kRedBlocksPerSm x its device's SM count).
+constexpr int kRedBlocksPerSm = 8;
 constexpr int kRedThreads = 256;
 constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3, energy)
 
@@ -53,16 +54,18 @@ cudaError_t launch_moments(int q, int storage, const void *f, const Grid &g, int
                            float *rho, float *u, float *pi1, cudaStream_t st);
 
 // Deterministic FP64 reduction of (sum drho, sum rho u, 0.5 sum rho |u|^2)
-// into partials [kRedBlocks][kRedValues], then into out[kRedValues].
+// into partials [nb][kRedValues], nb = min(max_blocks, cells / kRedThreads
+// rounded up), then into out[kRedValues]. The summation order depends only
+// on the grid and max_blocks, so results repeat bit for bit.
 cudaError_t launch_diagnostics(int q, int storage, const void *f, const Grid &g, int parity,
-                               double *partials, double *out, cudaStream_t st);
+                               int max_blocks, double *partials, double *out, cudaStream_t st);
 
 // 0.5 sum |curl u|^2 from a velocity field u [D][N] (central differences),
-// reduced through partials [kRedBlocks] into out[0]. With walls: second-order
+// reduced through partials [max_blocks at most] into out[0]. With walls: second-order
 // one-sided differences on the wall planes and the trapezoidal weights (1/2
 // per wall plane a node lies on).
-cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, double *partials, double *out,
-                             cudaStream_t st);
+cudaError_t launch_enstrophy(int d, const float *u, const Grid &g, int max_blocks,
+                             double *partials, double *out, cudaStream_t st);
 
 // As launch_diagnostics with the number of partial-sum blocks given by the
 // caller (partials must hold nblocks * kRedValues doubles); used by the

@@ -18,9 +18,17 @@
 // Every row a call reads is written earlier in the same call, so nothing has
 // to be cleared between calls.
 //
-// The device address of the array is looked up once per device, on the first
-// call made while that device is current (cudaGetSymbolAddress). Make that
-// first call before any stream capture on the device.
+// The device address of the array is looked up once per device and CUDA
+// context, on the first call made while that context is current
+// (cudaGetSymbolAddress); a new context on the device (after cudaDeviceReset,
+// or a context the caller created itself) is looked up again on its first
+// call. Make that first call before any stream capture on the device.
+//
+// The store must be device (or managed) memory of the current device: a host
+// pointer, or memory of another GPU, is rejected with LB_EINVAL before any
+// kernel could touch it (cudaPointerGetAttributes, which allocates nothing).
+#include <cuda.h>
+
 #include <cstring>
 #include <mutex>
 
@@ -38,28 +46,69 @@ static __device__ __align__(256) double g_scratch[(kRows + 1) * lbrr::kRedValues
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double *g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+  CUcontext ctx;  // the context the address was looked up in
+  double *addr;
+};
+ScratchSlot g_slot[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device (looked up once).
-int scratch_address(double **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess)
-    return lbrr::report_error(LB_ECUDA, "lb_diagnostics_static: no CUDA device (%s)",
-                              cudaGetErrorString(e));
+// The driver's cuCtxGetCurrent, found through the runtime (no link to libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(p);
+  }();
+  return fn;
+}
+
+// Device address of g_scratch in the current context of the current device
+// (looked up once per device and context).
+int scratch_address(int dev, double **out) {
   if (dev < 0 || dev >= kMaxDevices)
     return lbrr::report_error(LB_EINVAL, "lb_diagnostics_static: device %d out of range", dev);
+  CtxGetCurrentFn get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  if (!get || get(&ctx) != CUDA_SUCCESS || !ctx)
+    return lbrr::report_error(LB_ECUDA, "lb_diagnostics_static: no current CUDA context");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!g_slot[dev].addr || g_slot[dev].ctx != ctx) {
     void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p)
       return lbrr::report_error(LB_ECUDA,
                                 "lb_diagnostics_static: cudaGetSymbolAddress failed (%s)",
                                 cudaGetErrorString(e));
-    g_scratch_addr[dev] = static_cast<double *>(p);
+    g_slot[dev] = ScratchSlot{ctx, static_cast<double *>(p)};
   }
-  *out = g_scratch_addr[dev];
+  *out = g_slot[dev].addr;
+  return LB_OK;
+}
+
+// LB_OK when `store` is device or managed memory that the current device
+// `dev` can read as its own.
+int check_store(const void *store, int dev) {
+  cudaPointerAttributes a{};
+  cudaError_t e = cudaPointerGetAttributes(&a, store);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return lbrr::report_error(LB_EINVAL, "lb_diagnostics_static: the store is not CUDA memory (%s)",
+                              cudaGetErrorString(e));
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return lbrr::report_error(LB_EINVAL,
+                              "lb_diagnostics_static: the store must be device memory of the "
+                              "current device (got a host or unregistered pointer)");
+  if (a.type == cudaMemoryTypeDevice && a.device != dev)
+    return lbrr::report_error(LB_EINVAL,
+                              "lb_diagnostics_static: the store lives on device %d, the current "
+                              "device is %d",
+                              a.device, dev);
   return LB_OK;
 }
 
@@ -83,8 +132,15 @@ extern "C" int lb_diagnostics_static(int lattice, int nx, int ny, int nz, int st
                               "lb_diagnostics_static: %lld cells exceed the static scratch limit "
                               "of %lld cells (LB_STATIC_MAX_CELLS); use lb_diagnostics",
                               n, (long long)LB_STATIC_MAX_CELLS);
+  int dev = -1;
+  cudaError_t de = cudaGetDevice(&dev);
+  if (de != cudaSuccess)
+    return lbrr::report_error(LB_ECUDA, "lb_diagnostics_static: no CUDA device (%s)",
+                              cudaGetErrorString(de));
+  int rc = check_store(store, dev);
+  if (rc != LB_OK) return rc;
   double *scratch = nullptr;
-  int rc = scratch_address(&scratch);
+  rc = scratch_address(dev, &scratch);
   if (rc != LB_OK) return rc;
   const int nblocks = (int)((n + kCellsPerBlock - 1) / kCellsPerBlock);
   double *result = scratch + (long long)kRows * lbrr::kRedValues;

@@ -32,7 +32,11 @@ def _static(lib, s, buf, parity, storage, stream):
     (B.D3Q27, (40, 30, 20), B.STORE_F32),
     (B.D2Q9, (300, 7, 1), B.STORE_F32),
     (B.D3Q27, (24, 16, 12), B.STORE_F16),
+    (B.D3Q27, (24, 16, 12), B.STORE_BF16),
     (B.D3Q19, (40, 30, 20), B.STORE_F32),
+    # short rows, many of them: each of the 40 blocks strides over ~100
+    # partly filled 256-cell row chunks
+    (B.D3Q27, (40, 64, 64), B.STORE_F32),
 ])
 def test_static_diagnostics_match_lb_diagnostics(lattice, shape, storage):
     import torch
@@ -72,3 +76,17 @@ def test_static_diagnostics_rejects_grids_beyond_the_limit():
     assert "LB_STATIC_MAX_CELLS" in msg and str(B.LB_STATIC_MAX_CELLS) in msg
     rc = lib.lb_diagnostics_static(B.D2Q9, 16, 16, 2, B.STORE_F32, 0, dummy, out.ctypes.data, None)
     assert rc == B.LB_EINVAL
+
+
+@pytest.mark.gpu
+def test_static_diagnostics_rejects_memory_that_is_not_on_the_device():
+    """A host pointer (here numpy memory) never reaches a kernel: the call
+    inspects the pointer first and answers LB_EINVAL."""
+    build_mod.build()
+    lib = B.load()
+    host = np.zeros(27 * 8 * 8 * 8, dtype=np.float32)
+    out = np.zeros(5)
+    rc = lib.lb_diagnostics_static(B.D3Q27, 8, 8, 8, B.STORE_F32, 0, host.ctypes.data,
+                                   out.ctypes.data, None)
+    assert rc == B.LB_EINVAL
+    assert "device memory" in lib.lb_last_error(None).decode()
