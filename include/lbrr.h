@@ -250,6 +250,23 @@ LB_API int lb_mlp_forward(lb_mlp *mlp, const void *X, long long M, float *Y);
  * the loss into *loss (host, may be NULL); parameters unchanged. Deterministic. */
 LB_API int lb_mlp_gradients(lb_mlp *mlp, const void *X, const float *T, long long M, float *grad,
                             double *loss);
+/* Inspection forms of lb_mlp_forward and lb_mlp_gradients (no counterpart in
+ * the paper; they let a test check every layer of the network kernels, not
+ * only their end result). They run the same arithmetic and also write, for
+ * every row, the FP32 values the kernel computed before it rounded them to
+ * BF16 for the next product:
+ *   lb_mlp_forward_trace: H [M][128] (device): tanh(W1 x + b1) in columns
+ *     0..63, tanh(W2 h1 + b2) in columns 64..127 (h1 rounded to BF16);
+ *   lb_mlp_gradients_trace: trace [M][320] (device): h1 (0..63), h2 (64..127),
+ *     y (128..159), dy = 2 (y - t) / (17 M) on the used outputs (160..191),
+ *     dh2 = (W3^T dy) (1 - h2^2) (192..255, dy rounded to BF16), dh1 =
+ *     (W2^T dh2) (1 - h1^2) (256..319, dh2 rounded to BF16).
+ * The weight gradients are products of the BF16 roundings of these rows with
+ * the BF16 inputs (dW1 = dh1^T x, dW2 = dh2^T h1, dW3 = dy^T h2), the bias
+ * gradients sums of the FP32 values (db1 = sum dh1, ...). */
+LB_API int lb_mlp_forward_trace(lb_mlp *mlp, const void *X, long long M, float *Y, float *H);
+LB_API int lb_mlp_gradients_trace(lb_mlp *mlp, const void *X, const float *T, long long M,
+                                  float *grad, double *loss, float *trace);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
  * batch; *loss (host, may be NULL) is the loss before the step. */
 LB_API int lb_mlp_train_step(lb_mlp *mlp, const void *X, const float *T, long long M, float lr,

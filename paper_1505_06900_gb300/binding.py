@@ -56,6 +56,8 @@ SIGNATURES = {
     "lb_mlp_set_scaling": (_i, [_vp, _vp, _vp, _vp]),
     "lb_mlp_forward": (_i, [_vp, _vp, _ll, _vp]),
     "lb_mlp_gradients": (_i, [_vp, _vp, _vp, _ll, _vp, _vp]),
+    "lb_mlp_forward_trace": (_i, [_vp, _vp, _ll, _vp, _vp]),
+    "lb_mlp_gradients_trace": (_i, [_vp, _vp, _vp, _ll, _vp, _vp, _vp]),
     "lb_mlp_train_step": (_i, [_vp, _vp, _vp, _ll, ctypes.c_float, _vp]),
     "lb_closure_features": (_i, [_vp, _vp, _vp]),
     "lb_closure_targets": (_i, [_vp, _vp, _vp]),
@@ -333,22 +335,35 @@ class MLP:
                                                  a[2].ctypes.data))
         self.scaling = a
 
-    def forward(self, X):
+    def forward(self, X, trace: bool = False):
+        """Y [M][32]; with trace also H [M][128] (lb_mlp_forward_trace)."""
         import torch
         assert X.dtype == torch.bfloat16 and X.is_cuda and X.shape[1] == MLP_IN
         X = X.contiguous()
         Y = torch.empty((X.shape[0], MLP_OUT), device=X.device, dtype=torch.float32)
-        self._check(self._lib.lb_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
-        return Y
+        if not trace:
+            self._check(self._lib.lb_mlp_forward(self._h, _ptr(X), X.shape[0], _ptr(Y)))
+            return Y
+        H = torch.empty((X.shape[0], 128), device=X.device, dtype=torch.float32)
+        self._check(self._lib.lb_mlp_forward_trace(self._h, _ptr(X), X.shape[0], _ptr(Y),
+                                                   _ptr(H)))
+        return Y, H
 
-    def gradients(self, X, T):
+    def gradients(self, X, T, trace: bool = False):
+        """(gradient, loss); with trace also the trace rows [M][320]
+        (lb_mlp_gradients_trace)."""
         import torch
         X, T = X.contiguous(), T.contiguous()
         g = torch.empty(MLP_PARAMS, device=X.device, dtype=torch.float32)
         loss = ctypes.c_double()
-        self._check(self._lib.lb_mlp_gradients(self._h, _ptr(X), _ptr(T), X.shape[0], _ptr(g),
-                                               ctypes.byref(loss)))
-        return g, loss.value
+        if not trace:
+            self._check(self._lib.lb_mlp_gradients(self._h, _ptr(X), _ptr(T), X.shape[0],
+                                                   _ptr(g), ctypes.byref(loss)))
+            return g, loss.value
+        tr = torch.empty((X.shape[0], 320), device=X.device, dtype=torch.float32)
+        self._check(self._lib.lb_mlp_gradients_trace(self._h, _ptr(X), _ptr(T), X.shape[0],
+                                                     _ptr(g), ctypes.byref(loss), _ptr(tr)))
+        return g, loss.value, tr
 
     def train_step(self, X, T, lr: float, want_loss: bool = True):
         X, T = X.contiguous(), T.contiguous()

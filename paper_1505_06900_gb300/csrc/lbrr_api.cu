@@ -671,27 +671,34 @@ int lb_mlp_set_scaling(lb_mlp *m, const float *in_mean, const float *in_inv_std,
   return LB_OK;
 }
 
-int lb_mlp_forward(lb_mlp *m, const void *X, long long M, float *Y) {
+static int mlp_forward(lb_mlp *m, const void *X, long long M, float *Y, float *H) {
   if (!m || !X || !Y || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
   DeviceGuard dg(m->device);
-  const long long tiles = (M + 63) / 64;
-  const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
-  (void)nb;
   cudaError_t e =
-      lbrr::launch_mlp_tc(m->d, X, nullptr, nullptr, M, Y, m->status, m->nblocks, m->stream);
+      lbrr::launch_mlp_tc(m->d, X, nullptr, nullptr, M, Y, m->status, m->nblocks, m->stream, H);
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "forward: %s", cudaGetErrorString(e));
   return mlp_status(m, m->stream);
 }
 
+int lb_mlp_forward(lb_mlp *m, const void *X, long long M, float *Y) {
+  return mlp_forward(m, X, M, Y, nullptr);
+}
+
+int lb_mlp_forward_trace(lb_mlp *m, const void *X, long long M, float *Y, float *H) {
+  if (!H) return mlp_fail(m, LB_EINVAL, "null activation buffer");
+  return mlp_forward(m, X, M, Y, H);
+}
+
 static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
-                        int adam, float lr, double *loss) {
+                        int adam, float lr, double *loss, float *trace = nullptr) {
   if (!m || !X || !T || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
   if (adam && !(lr > 0.f && std::isfinite(lr)))
     return mlp_fail(m, LB_EINVAL, "learning rate must be positive");
   DeviceGuard dg(m->device);
   const long long tiles = (M + 63) / 64;
   const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
-  cudaError_t e = lbrr::launch_mlp(m->d, X, T, M, nullptr, m->gpart, m->lpart, nb, m->stream);
+  cudaError_t e =
+      lbrr::launch_mlp(m->d, X, T, M, nullptr, m->gpart, m->lpart, nb, m->stream, trace);
   float bc1 = 1.f, bc2 = 1.f;
   if (adam) {
     const long long t = m->t + 1;
@@ -716,6 +723,12 @@ int lb_mlp_gradients(lb_mlp *m, const void *X, const float *T, long long M, floa
                      double *loss) {
   if (!grad) return mlp_fail(m, LB_EINVAL, "null gradient buffer");
   return mlp_backward(m, X, T, M, grad, 0, 0.f, loss);
+}
+
+int lb_mlp_gradients_trace(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
+                           double *loss, float *trace) {
+  if (!grad || !trace) return mlp_fail(m, LB_EINVAL, "null gradient or trace buffer");
+  return mlp_backward(m, X, T, M, grad, 0, 0.f, loss, trace);
 }
 
 int lb_mlp_train_step(lb_mlp *m, const void *X, const float *T, long long M, float lr,

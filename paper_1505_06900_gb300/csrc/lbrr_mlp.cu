@@ -108,11 +108,27 @@ __device__ __forceinline__ void wgrad(const __nv_bfloat16 (*Ls)[LDL], int j0,
   }
 }
 
-template <bool TRAIN>
+// Trace rows (TRACE instantiation): FP32 values of row r at trace[r][c] for
+// the columns col0 + 8 nt + 2 t (+1) of NT accumulator tiles.
+template <int NT>
+__device__ __forceinline__ void trace_tile(float *__restrict__ trace, long long ra, long long rb,
+                                           long long M, int col0, int t,
+                                           const float (&acc)[NT][4]) {
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int c = col0 + 8 * nt + 2 * t;
+    if (ra < M)
+      *reinterpret_cast<float2 *>(trace + ra * kMlpTrace + c) = make_float2(acc[nt][0], acc[nt][1]);
+    if (rb < M)
+      *reinterpret_cast<float2 *>(trace + rb * kMlpTrace + c) = make_float2(acc[nt][2], acc[nt][3]);
+  }
+}
+
+template <bool TRAIN, bool TRACE = false>
 __global__ void __launch_bounds__(kThreads)
     mlp_kernel(MlpDevice p, const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T,
                long long M, float *__restrict__ Y, float *__restrict__ gpart,
-               float *__restrict__ lpart) {
+               float *__restrict__ lpart, float *__restrict__ trace) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem &s = *reinterpret_cast<TrainSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -157,6 +173,8 @@ __global__ void __launch_bounds__(kThreads)
     }
     uint32_t a1[4][4];
     act_to_frags<8>(h1, p.b1, t, a1);
+    const long long ra = row0 + r0 + g, rb = ra + 8;
+    if (TRACE) trace_tile<8>(trace, ra, rb, M, kTraceH1, t, h1);
     // ---- layer 2
     float h2[8][4] = {};
 #pragma unroll
@@ -169,6 +187,7 @@ __global__ void __launch_bounds__(kThreads)
       }
     uint32_t a2[4][4];
     act_to_frags<8>(h2, p.b2, t, a2);
+    if (TRACE) trace_tile<8>(trace, ra, rb, M, kTraceH2, t, h2);
     // ---- layer 3
     float y[4][4] = {};
 #pragma unroll
@@ -179,7 +198,6 @@ __global__ void __launch_bounds__(kThreads)
         b_frag(b0, b1, p.w3, kMlpHidden, 8 * nt, 16 * ks, g, t);
         mma16816(y[nt], a2[ks], b0, b1);
       }
-    const long long ra = row0 + r0 + g, rb = ra + 8;
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       const int c = 8 * nt + 2 * t;
@@ -188,6 +206,7 @@ __global__ void __launch_bounds__(kThreads)
       y[nt][2] += p.b3[c];
       y[nt][3] += p.b3[c + 1];
     }
+    if (TRACE) trace_tile<4>(trace, ra, rb, M, kTraceY, t, y);
     if (!TRAIN) {
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
@@ -213,6 +232,7 @@ __global__ void __launch_bounds__(kThreads)
         dy[nt][e] = 2.0f * d * inv_n;
       }
     }
+    if (TRACE) trace_tile<4>(trace, ra, rb, M, kTraceDy, t, dy);
     uint32_t ady[2][4];
     to_frags<4>(dy, ady);
     // ---- dh2 = (dy W3) * (1 - h2^2), with W3^T [64][32] K-major
@@ -229,6 +249,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) g2[nt][e] *= 1.0f - h2[nt][e] * h2[nt][e];
+    if (TRACE) trace_tile<8>(trace, ra, rb, M, kTraceDh2, t, g2);
     uint32_t ag2[4][4];
     to_frags<8>(g2, ag2);
     // ---- dh1 = (dh2 W2) * (1 - h1^2), with W2^T [64][64]
@@ -245,6 +266,7 @@ __global__ void __launch_bounds__(kThreads)
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int e = 0; e < 4; ++e) g1[nt][e] *= 1.0f - h1[nt][e] * h1[nt][e];
+    if (TRACE) trace_tile<8>(trace, ra, rb, M, kTraceDh1, t, g1);
 
     // ---- stage the BF16 tiles for the weight gradients, bias gradients per warp
     store_tile<8, kHs>(s.h1, r0, g, t, h1);
@@ -340,18 +362,16 @@ __device__ void mlp_refresh_one(MlpDevice p, int k, float w) {
 size_t mlp_train_smem() { return sizeof(TrainSmem); }
 
 cudaError_t launch_mlp(const MlpDevice &p, const void *X, const float *T, long long M, float *Y,
-                       float *gpart, float *lpart, int nblocks, cudaStream_t st) {
+                       float *gpart, float *lpart, int nblocks, cudaStream_t st, float *trace) {
   const size_t smem = sizeof(TrainSmem);
   const bool train = T != nullptr;
-  cudaError_t e = cudaFuncSetAttribute(train ? mlp_kernel<true> : mlp_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (trace && !train) return cudaErrorInvalidValue;
+  auto kern = trace ? mlp_kernel<true, true> : (train ? mlp_kernel<true> : mlp_kernel<false>);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (train)
-    mlp_kernel<true><<<nblocks, kThreads, smem, st>>>(
-        p, static_cast<const __nv_bfloat16 *>(X), T, M, Y, gpart, lpart);
-  else
-    mlp_kernel<false><<<nblocks, kThreads, smem, st>>>(
-        p, static_cast<const __nv_bfloat16 *>(X), T, M, Y, gpart, lpart);
+  kern<<<nblocks, kThreads, smem, st>>>(p, static_cast<const __nv_bfloat16 *>(X), T, M, Y, gpart,
+                                       lpart, trace);
   return cudaGetLastError();
 }
 

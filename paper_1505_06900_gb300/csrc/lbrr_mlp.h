@@ -115,10 +115,19 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
 
 size_t mlp_train_smem();
 
+// Columns of one trace row of the training kernel (FP32, as computed, before
+// any BF16 rounding): layer-1 and layer-2 activations, outputs, the loss
+// gradient dy = 2 (y - t) / (17 M) on the used outputs, and the back-propagated
+// dh2 = (W3^T dy) (1 - h2^2), dh1 = (W2^T dh2) (1 - h1^2).
+constexpr int kTraceH1 = 0, kTraceH2 = 64, kTraceY = 128, kTraceDy = 160, kTraceDh2 = 192,
+              kTraceDh1 = 256, kMlpTrace = 320;
+
 // Forward (T == nullptr: writes Y [M][32]) or forward + backward (writes the
-// block partial gradients gpart [nblocks][kMlpParams] and losses lpart).
+// block partial gradients gpart [nblocks][kMlpParams] and losses lpart); with
+// trace (backward only) also the trace rows [M][kMlpTrace].
 cudaError_t launch_mlp(const MlpDevice &p, const void *X, const float *T, long long M, float *Y,
-                       float *gpart, float *lpart, int nblocks, cudaStream_t st);
+                       float *gpart, float *lpart, int nblocks, cudaStream_t st,
+                       float *trace = nullptr);
 // Gradient = sum of the partials; optional Adam step (bias corrections bc1,
 // bc2); loss = sum of the block losses (double, device) when loss_out != null.
 cudaError_t launch_mlp_reduce(const MlpDevice &p, const float *gpart, int nparts, float *grad_out,
@@ -142,8 +151,11 @@ cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int pa
 // rows are the cells of grid *g, features from the moment field, outputs the
 // 17 standardised predictions Y [17][N]. Without: rows X [M][288] BF16, Y
 // [M][32]. *status becomes 1 if a tensor-core wait timed out.
+// With H (rows X only): also the FP32 activations of layers 1 and 2 of
+// every row, H [M][128], as computed before their BF16 rounding.
 cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, const Grid *g,
-                          long long M, float *Y, int *status, int nblocks, cudaStream_t st);
+                          long long M, float *Y, int *status, int nblocks, cudaStream_t st,
+                          float *H = nullptr);
 // The TMA-fed, pipelined forward pass (lbrr_mlp_conv.cu) for grids whose
 // rows are whole 128-cell tiles: the feature source xs (standardised moments,
 // BF16, 16 channels, one-cell periodic halo: feature_source_bytes(g) bytes),

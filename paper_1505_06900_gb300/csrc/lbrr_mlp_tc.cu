@@ -57,20 +57,28 @@ constexpr uint32_t kTcSmem = kOffMs + kMsBytes;
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) { return pack_bf16(lo, hi); }
 
 // Layer epilogue: tanh(acc + bias) of 32 of the 64 columns (half 0 or 1) into
-// row r of a K = 64 operand.
+// row r of a K = 64 operand; with TRACE also the FP32 values into hrow[64].
+template <bool TRACE = false>
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, const float *bias,
-                                                unsigned char *dst, int r, int half) {
+                                                unsigned char *dst, int r, int half,
+                                                float *hrow = nullptr) {
 #pragma unroll
   for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
     float v[16];
     tmem_ld16(taddr + c0, v);
 #pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = tanh_approx(v[k] + bias[c0 + k]);
+    if (TRACE && hrow)
+#pragma unroll
+      for (int k = 0; k < 16; k += 4)
+        *reinterpret_cast<float4 *>(hrow + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+#pragma unroll
     for (int k = 0; k < 16; k += 8) {
       uint4 q;
-      q.x = pack2(tanh_approx(v[k] + bias[c0 + k]), tanh_approx(v[k + 1] + bias[c0 + k + 1]));
-      q.y = pack2(tanh_approx(v[k + 2] + bias[c0 + k + 2]), tanh_approx(v[k + 3] + bias[c0 + k + 3]));
-      q.z = pack2(tanh_approx(v[k + 4] + bias[c0 + k + 4]), tanh_approx(v[k + 5] + bias[c0 + k + 5]));
-      q.w = pack2(tanh_approx(v[k + 6] + bias[c0 + k + 6]), tanh_approx(v[k + 7] + bias[c0 + k + 7]));
+      q.x = pack2(v[k], v[k + 1]);
+      q.y = pack2(v[k + 2], v[k + 3]);
+      q.z = pack2(v[k + 4], v[k + 5]);
+      q.w = pack2(v[k + 6], v[k + 7]);
       *reinterpret_cast<uint4 *>(dst + cm_offset(r, c0 + k, kMlpHidden)) = q;
     }
   }
@@ -148,11 +156,13 @@ __device__ __forceinline__ void features_gather(const MlpDevice &p, const float 
 // When nx is a multiple of 128 a tile is one row segment and the 9 x 10
 // moment rows around it are first staged in shared memory with 16-byte loads.
 // Otherwise rows are X [M][288] (BF16) and outputs Y [M][32].
-template <bool FROM_MOM>
+// TRACE (rows X only): also H[row][0..63] and H[row][64..127], the FP32
+// activations of layers 1 and 2 before their BF16 rounding.
+template <bool FROM_MOM, bool TRACE = false>
 __global__ void __launch_bounds__(kTcThreads, 1)
     mlp_tc_kernel(MlpDevice p, const __nv_bfloat16 *__restrict__ X,
                   const float *__restrict__ mom, const Grid g, long long M,
-                  float *__restrict__ Y, int *status) {
+                  float *__restrict__ Y, int *status, float *__restrict__ H) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int r = tid & (kTcRows - 1), half = tid >> 7;  // row, and which half of its work
@@ -284,7 +294,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     phase ^= 1;
     fence_after();
     if (!ok) break;
-    hidden_epilogue(lane_addr + 0, sb, smem + kOffSA2, r, half);
+    hidden_epilogue<TRACE>(lane_addr + 0, sb, smem + kOffSA2, r, half,
+                           TRACE && valid ? H + row * (2 * kMlpHidden) : nullptr);
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -301,7 +312,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     phase ^= 1;
     fence_after();
     if (!ok) break;
-    hidden_epilogue(lane_addr + 64, sb + kMlpHidden, smem + kOffSA3, r, half);
+    hidden_epilogue<TRACE>(lane_addr + 64, sb + kMlpHidden, smem + kOffSA3, r, half,
+                           TRACE && valid ? H + row * (2 * kMlpHidden) + kMlpHidden : nullptr);
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -357,19 +369,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }  // namespace
 
 cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, const Grid *g,
-                          long long M, float *Y, int *status, int nblocks, cudaStream_t st) {
+                          long long M, float *Y, int *status, int nblocks, cudaStream_t st,
+                          float *H) {
   const bool from_mom = mom != nullptr;
-  cudaError_t e = cudaFuncSetAttribute(from_mom ? mlp_tc_kernel<true> : mlp_tc_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (from_mom && H) return cudaErrorInvalidValue;
+  auto kern = from_mom ? mlp_tc_kernel<true> : (H ? mlp_tc_kernel<false, true>
+                                                  : mlp_tc_kernel<false>);
+  cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   const long long tiles = (M + kTcRows - 1) / kTcRows;
   const int nb = (int)(tiles < nblocks ? tiles : nblocks);
   const Grid gg = g ? *g : Grid{1, 1, 1, M};
-  if (from_mom)
-    mlp_tc_kernel<true><<<nb, kTcThreads, kTcSmem, st>>>(p, nullptr, mom, gg, M, Y, status);
-  else
-    mlp_tc_kernel<false><<<nb, kTcThreads, kTcSmem, st>>>(
-        p, static_cast<const __nv_bfloat16 *>(X), nullptr, gg, M, Y, status);
+  kern<<<nb, kTcThreads, kTcSmem, st>>>(p, static_cast<const __nv_bfloat16 *>(X), mom, gg, M, Y,
+                                        status, H);
   return cudaGetLastError();
 }
 
