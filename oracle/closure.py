@@ -10,10 +10,23 @@ the learned-closure extension built around the RR step:
   xx, xy, xz, yy, yz, zz) of the cell and of its 26 periodic neighbours,
   standardised per moment kind, neighbour index (dx+1) + 3(dy+1) + 9(dz+1),
   feature index 10 * neighbour + moment, zero padded to 288;
-* target: the Hermite coefficients of orders 3..6 of the cell's populations
-  minus those of the RR reconstruction f0 + f1 from the cell's own moments
-  (the order-2 difference is zero by construction), 17 values, standardised
-  per coefficient and zero padded to 32;
+* target (a priori form): the Hermite coefficients of orders 3..6 of the
+  cell's populations minus those of the RR reconstruction f0 + f1 from the
+  cell's own moments (the order-2 difference is zero by construction), 17
+  values, standardised per coefficient and zero padded to 32;
+* target (step-matching form): the correction of orders 3..6 that makes one
+  coarse RR update of a coarse state A reproduce a coarse state B two fine
+  steps later: the post-collision populations that streaming would carry into
+  B are P_i(x) = B_i(x + xi_i); R = the RR post-collision of A; the target is
+  the order 3..6 Hermite coefficients of (P - R) divided by (1 - 1/tau), since
+  the closure adds its prediction to the off-equilibrium coefficients before
+  the relaxation;
+* coarsening with a rescaled off-equilibrium part: the box average fbar,
+  then f0(rho, u) + s (fbar - f0(rho, u)) with rho, u the moments of fbar.
+  With s = 2 tau_c / tau_f the coarse state carries the off-equilibrium part
+  a coarse run builds itself: the constitutive relation of Sec. 3.3,
+  a1^(2) = -2 c_s^2 rho tau S, holds on each grid in its own lattice units,
+  where the strain rate per coarse step and cell is twice the fine one;
 * the network: y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3 with W1 [64 x 288],
   W2 [64 x 64], W3 [32 x 64]; loss = mean over samples and the 17 used outputs
   of (y - t)^2; analytic backward; Adam (beta1 0.9, beta2 0.999, eps 1e-8,
@@ -113,6 +126,42 @@ def moment_field(f: np.ndarray) -> np.ndarray:
     q, nz, ny, nx = f.shape
     rho, u, pi = fields(D3Q27, (nx, ny, nz), f)
     return np.concatenate([(rho - 1.0)[None], u, pi], axis=0)
+
+
+def coarsen_neq(f: np.ndarray, scale: float) -> np.ndarray:
+    """2x2x2 box average of f [Q, nz, ny, nx] with the off-equilibrium part
+    scaled by `scale`: f0(rho, u) + scale (fbar - f0(rho, u))."""
+    fb = coarsen(f)
+    q, nz, ny, nx = fb.shape
+    rho, u, _ = fields(D3Q27, (nx, ny, nz), fb)
+    out = np.empty_like(fb).reshape(q, -1)
+    fbf, rr, uu = fb.reshape(q, -1), rho.reshape(-1), u.reshape(3, -1)
+    for c in range(nx * ny * nz):
+        f0 = feq_cell(D3Q27, rr[c], uu[:, c])
+        out[:, c] = f0 + scale * (fbf[:, c] - f0)
+    return out.reshape(fb.shape)
+
+
+def step_targets(f_pre: np.ndarray, f_post: np.ndarray, tau: float) -> np.ndarray:
+    """Unstandardised step-matching targets [N, 17]: orders 3..6 of
+    (P - R) / (1 - 1/tau) per cell, P_i(x) = f_post_i(x + xi_i) the populations
+    streaming would carry into f_post, R the RR post-collision of f_pre."""
+    from . import collide_cell, lattice_tables
+    q, nz, ny, nx = f_pre.shape
+    H, _ = hermite_basis(D3Q27)
+    Hhi = H[10:27]
+    cvel, _ = lattice_tables(D3Q27)
+    P = np.empty_like(f_post)
+    for i in range(q):
+        # value at x of the field shifted back by xi_i: f_post_i(x + xi_i)
+        P[i] = np.roll(f_post[i], shift=(-cvel[i, 2], -cvel[i, 1], -cvel[i, 0]), axis=(0, 1, 2))
+    pre, P = f_pre.reshape(q, -1), P.reshape(q, -1)
+    out = np.zeros((nx * ny * nz, N_OUT_USED))
+    om1 = 1.0 - 1.0 / tau
+    for c in range(nx * ny * nz):
+        R = collide_cell(D3Q27, pre[:, c], tau)
+        out[c] = Hhi @ (P[:, c] - R) / om1
+    return out
 
 
 def features(mom: np.ndarray, mean: np.ndarray, inv_std: np.ndarray) -> np.ndarray:

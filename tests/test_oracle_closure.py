@@ -152,3 +152,97 @@ def test_step_closure_with_zero_network_is_rr():
     p = C.unpack(np.zeros(C.N_PARAMS))
     got = C.step_closure(f, tau, p, np.zeros(10), np.ones(10), np.ones(17))
     assert np.abs(got - O.step(O.D3Q27, shape, tau, f, 1)).max() < 1e-16
+
+
+# ----------------------------------------- step-matching targets, coarsening --
+def _random_state(shape, seed, amp=0.03):
+    """Positive D3Q27 populations near rest with every Hermite mode excited."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    _, w = O.lattice_tables(O.D3Q27)
+    return w[:, None, None, None] * (1.0 + amp * rng.standard_normal((27, nz, ny, nx)))
+
+
+def _stream(post):
+    cvel, _ = O.lattice_tables(O.D3Q27)
+    out = np.empty_like(post)
+    for i in range(27):
+        out[i] = np.roll(post[i], shift=(cvel[i, 2], cvel[i, 1], cvel[i, 0]), axis=(0, 1, 2))
+    return out
+
+
+def test_step_targets_vanish_on_a_plain_rr_update():
+    """If B is the plain RR update of A, no correction is needed: every target
+    is zero (to round-off), whatever the state (brute force against the
+    oracle's own collide-and-stream)."""
+    shape, tau = (5, 4, 3), 0.63
+    f = _random_state(shape, 10)
+    g = O.step(O.D3Q27, shape, tau, f, 1)
+    t = C.step_targets(f, g, tau)
+    assert np.abs(t).max() < 1e-13
+
+
+def test_step_targets_recover_a_planted_correction():
+    """If B is A collided with a known correction delta (orders 3..6 added to
+    the off-equilibrium coefficients before the relaxation, the oracle's
+    closure collision) and streamed, the targets are delta, cell by cell."""
+    shape, tau = (4, 5, 3), 0.58
+    f = _random_state(shape, 11)
+    rng = np.random.default_rng(12)
+    n = int(np.prod(shape))
+    delta = 1e-3 * rng.standard_normal((n, C.N_OUT_USED))
+    ff = f.reshape(27, -1)
+    post = np.stack([O.collide_cell_closure(ff[:, c], tau, delta[c]) for c in range(n)], axis=1)
+    g = _stream(post.reshape(f.shape))
+    t = C.step_targets(f, g, tau)
+    assert np.abs(t - delta).max() < 1e-13
+
+
+def test_coarsen_neq_keeps_moments_and_scales_the_off_equilibrium_part():
+    shape = (4, 6, 2)
+    f = _random_state((8, 12, 4), 13)
+    fb = C.coarsen(f)
+    assert np.abs(C.coarsen_neq(f, 1.0) - fb).max() < 1e-15
+    H, _ = O.hermite_basis(O.D3Q27)
+    rho, u, _ = O.fields(O.D3Q27, shape, fb)
+    n = int(np.prod(shape))
+    f0 = np.stack([O.feq_cell(O.D3Q27, rho.reshape(-1)[c], u.reshape(3, -1)[:, c])
+                   for c in range(n)], axis=1)
+    for s in (0.0, 1.7, 2.0):
+        g = C.coarsen_neq(f, s)
+        r2, u2, _ = O.fields(O.D3Q27, shape, g)
+        assert np.abs(r2 - rho).max() < 1e-14 and np.abs(u2 - u).max() < 1e-14
+        # every Hermite coefficient of the off-equilibrium part scales by s
+        a = H @ (fb.reshape(27, -1) - f0)
+        b = H @ (g.reshape(27, -1) - f0)
+        assert np.abs(b - s * a).max() < 1e-14
+    assert np.abs(C.coarsen_neq(f, 0.0).reshape(27, -1) - f0).max() < 1e-15
+
+
+def test_coarsen_neq_scale_matches_the_constitutive_relation_on_the_coarse_grid():
+    """Sec. 3.3: a1^(2) = -2 c_s^2 rho tau S in lattice units. A fine shear
+    wave u_x = U sin(2 pi y / L), initialised with that off-equilibrium part at
+    tau_f, box-filtered with s = 2 tau_c / tau_f carries the coarse grid's own
+    relation at tau_c (S per coarse cell is twice S per fine cell); with s = 1
+    the filtered Pi^(1) is tau_f / (2 tau_c) of it (here 0.62)."""
+    nf, U = 32, 0.02
+    nc = nf // 2
+    tau_f = 0.8
+    tau_c = 0.5 + (tau_f - 0.5) / 2
+    y = (np.arange(nf) + 0.5) / nf
+    u = np.zeros((3, 2, nf, 2))
+    u[0] = U * np.sin(2 * np.pi * y)[None, :, None]
+    rho = np.ones((2, nf, 2))
+    f = O.init(O.D3Q27, (2, nf, 2), tau_f, rho, u, O.INIT_EQ_NEQ_FD)
+    yc = (np.arange(nc) + 0.5) / nc
+    s_xy = 0.5 * U * (2 * np.pi / nc) * np.cos(2 * np.pi * yc)  # du_x/dy per coarse cell / 2
+    want = -2.0 * (1.0 / 3.0) * tau_c * s_xy
+    for scale, tol in ((2 * tau_c / tau_f, 0.02), (1.0, None)):
+        g = C.coarsen_neq(f, scale)
+        _, _, pi = O.fields(O.D3Q27, (1, nc, 1), g)
+        got = pi[1, 0, :, 0]  # xy
+        err = np.abs(got - want).max() / np.abs(want).max()
+        if tol is not None:
+            assert err < tol, err
+        else:
+            assert err > 0.3, err
