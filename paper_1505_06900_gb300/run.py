@@ -3,6 +3,7 @@ its diagnostics history as JSON lines.
 
     python -m paper_1505_06900_gb300.run tgv3d --sizes 256 --machs 0.1 --steps 5000 \
         [--every 50] [--storage f16] [--out history.jsonl]
+    python -m paper_1505_06900_gb300.run tgv3d_lowprec --compare f32,f16,bf16 [--sizes 512]
     python -m paper_1505_06900_gb300.run --list
 
 One line per sample: step, convective time, mass, momentum, kinetic energy
@@ -77,6 +78,65 @@ def run_one(r: C.Run, emit) -> dict:
     return summary
 
 
+def compare_storages(r: C.Run, storages, emit) -> dict:
+    """The same run in several storage precisions side by side, in lock step:
+    every `every` updates one line per sample with each store's kinetic energy
+    and enstrophy and, for every store after the first (the reference, FP32
+    normally), the relative L2 difference of its velocity field from the
+    reference's; then a summary with the largest differences over the run."""
+    import torch
+    tau = r.tau()
+    rho, u = r.fields()
+    rho_d = torch.from_numpy(rho.astype(np.float32)).cuda()
+    u_d = torch.from_numpy(u.astype(np.float32)).cuda()
+    solvers = [B.Solver(r.lattice, r.shape, tau, storage=C.STORAGE[st]) for st in storages]
+    worst = {st: {"u_rel_l2": 0.0, "ke_rel": 0.0, "enstrophy_rel": 0.0} for st in storages[1:]}
+    try:
+        for s in solvers:
+            s.init_fields(rho_d, u_d)
+        del rho_d, u_d
+        done = 0
+        while True:
+            line = {"config": r.config, "n": r.n, "mach": r.mach, "step": done,
+                    "t": convective_time(r, done)}
+            ref_u = None
+            ref = {}
+            for st, s in zip(storages, solvers):
+                d = s.diagnostics()
+                ens = s.enstrophy()
+                _, uu, _ = s.moments()
+                line[st] = {"kinetic_energy": d[-1], "enstrophy": ens, "mass": d[0]}
+                if ref_u is None:
+                    ref_u, ref = uu, line[st]
+                    continue
+                du = float(torch.linalg.vector_norm(uu - ref_u) / torch.linalg.vector_norm(ref_u))
+                dke = d[-1] / ref["kinetic_energy"] - 1.0
+                dens = ens / ref["enstrophy"] - 1.0
+                line[st].update({"u_rel_l2_vs_" + storages[0]: du, "ke_rel_vs_" + storages[0]: dke,
+                                 "enstrophy_rel_vs_" + storages[0]: dens})
+                w = worst[st]
+                w["u_rel_l2"] = max(w["u_rel_l2"], du)
+                w["ke_rel"] = max(w["ke_rel"], abs(dke))
+                w["enstrophy_rel"] = max(w["enstrophy_rel"], abs(dens))
+                del uu
+            del ref_u
+            emit(line)
+            if done >= r.steps:
+                break
+            k = min(r.every, r.steps - done)
+            for s in solvers:
+                s.step(k)
+            done += k
+    finally:
+        for s in solvers:
+            s.close()
+    summary = {"config": r.config, "summary": True, "n": r.n, "mach": r.mach, "re": r.re,
+               "tau": tau, "steps": r.steps, "reference": storages[0], "max_over_run": worst,
+               "final": {st: line[st] for st in storages}}
+    emit(summary)
+    return summary
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("config", nargs="?")
@@ -86,6 +146,8 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int)
     ap.add_argument("--every", type=int)
     ap.add_argument("--storage", choices=sorted(C.STORAGE))
+    ap.add_argument("--compare", help="comma-separated storages run side by side, the first "
+                                      "the reference (e.g. f32,f16,bf16)")
     ap.add_argument("--out", help="JSON-lines file (default: stdout)")
     args = ap.parse_args(argv)
     if args.list or not args.config:
@@ -101,7 +163,10 @@ def main(argv=None) -> int:
             fh.write(json.dumps(obj) + "\n")
             fh.flush()
         for r in runs:
-            run_one(r, emit)
+            if args.compare:
+                compare_storages(r, args.compare.split(","), emit)
+            else:
+                run_one(r, emit)
     finally:
         if args.out:
             fh.close()
