@@ -304,16 +304,23 @@ CLOSURE_FLOP_PER_CELL = 2 * (288 * 64 + 64 * 64 + 64 * 32)
 
 def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms_per_step,
                     sampler=None):
-    """Train the closure on the filtered 128^3 study (seconds), then time the
-    closure step on an n_coarse^3 grid (one coarse step stands for two fine
-    steps of the 2 n_coarse grid) next to plain RR on the same coarse grid."""
+    """The learned-closure recipe at the configuration's sizes: fine
+    (2 n_coarse)^3 Taylor-Green runs (Ma 0.3, Re 1600) of eight seeded phases
+    give the training data, the network is trained by the library's kernels,
+    and the coarse runs with and without it start from the held-out phase's
+    filtered state and are judged against its filtered fine run after 400
+    coarse steps. Then the closure step is timed on the n_coarse^3 grid (one
+    coarse step stands for two fine steps) next to plain RR on the same grid."""
     from paper_1505_06900_gb300 import closure as CL
     from paper_1505_06900_gb300 import workloads as W
+    n_fine, coarse_steps = 2 * n_coarse, 400
     t0 = time.perf_counter()
-    net, rep = CL.study(n_fine=128, steps=1500, coarse_steps=400,
-                        snapshots=(200, 400, 600, 800))
+    net, scaling, rep = CL.study(n_fine=n_fine, steps=1500, coarse_steps=coarse_steps,
+                                 snapshots=CL.dense_snapshots(2 * coarse_steps, 48),
+                                 fraction=min(0.25, 2.5e6 / (n_coarse ** 3 * 17 * 8)),
+                                 every=100)
     train_s = time.perf_counter() - t0
-    tau_c = CL.coarse_tau(W.taylor_green_3d_tau(2 * n_coarse, MACH, RE))
+    tau_c = CL.coarse_tau(W.taylor_green_3d_tau(n_fine, MACH, RE))
     rho, u = W.taylor_green_3d(n_coarse, MACH)
     rho_d = torch.from_numpy(rho.astype(np.float32)).cuda()
     u_d = torch.from_numpy(u.astype(np.float32)).cuda()
@@ -343,11 +350,14 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
         "fallback_cell_updates": ml["fallbacks"],
         "u_error_vs_filtered_fine": rep["err_closure"],
         "coarse_rr_u_error_vs_filtered_fine": rep["err_rr"],
+        "u_error_history": rep["history"],
         "error_sizes": f"D3Q27 Taylor-Green Ma {rep['mach']} Re {rep['re']:g}, fine "
-                       f"{rep['n_fine']}^3 -> coarse {rep['n_fine'] // 2}^3, held-out phase, "
-                       f"{rep['coarse_steps']} coarse steps",
+                       f"{n_fine}^3 -> coarse {n_coarse}^3, held-out phase (seed 9), "
+                       f"{coarse_steps} coarse steps; history: (coarse steps, coarse RR, "
+                       f"closure) relative L2 of u",
         "training": {"samples": rep["samples"], "loss_first": rep["loss_first"],
-                     "loss_last": rep["loss_last"], "seconds": train_s},
+                     "loss_last": rep["loss_last"], "seconds": train_s,
+                     "gain": rep["gain"], "fallbacks_in_evaluation": rep["fallbacks"]},
     }
 
 

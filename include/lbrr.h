@@ -279,6 +279,25 @@ LB_API int lb_closure_targets(lb_ctx *ctx, const lb_mlp *mlp, float *T);
  * contexts, fine = 2 x coarse in every direction); resets coarse's step count.
  * The coarse grid of an acoustically scaled run uses tau_c = 1/2 + (tau_f - 1/2)/2. */
 LB_API int lb_coarsen(lb_ctx *fine, lb_ctx *coarse);
+/* The same with the off-equilibrium part of each averaged cell scaled:
+ * f0(rho, u) + neq_scale (fbar - f0(rho, u)), rho and u the moments of the
+ * average fbar. With neq_scale = 2 tau_coarse / tau_fine the coarse state
+ * carries the off-equilibrium part the coarse grid's own dynamics builds
+ * (the constitutive relation a1^(2) = -2 c_s^2 rho tau S of Sec. 3.3 in each
+ * grid's lattice units; the strain rate per coarse cell and step is twice the
+ * fine one). neq_scale = 1 is lb_coarsen. */
+LB_API int lb_coarsen_neq(lb_ctx *fine, lb_ctx *coarse, double neq_scale);
+/* Step-matching targets (extension, not in the paper): for two states of the
+ * same periodic D3Q27 FP32 RR grid, `pre` at some time and `post` one coarse
+ * update later in the reference run (e.g. the filtered fine run two fine
+ * steps later), T [N][32] (device) holds per cell the order 3..6 Hermite
+ * coefficients of (P - R) / (1 - 1/tau), P_i(x) = post_i(x + xi_i) the
+ * populations streaming carries into post, R the RR post-collision of pre
+ * (tau of pre), each divided by the network's out_scale and zero padded: the
+ * correction that, added to the recursion's coefficients before the
+ * relaxation (lb_set_closure), would make the RR update of pre reproduce
+ * those coefficients of post. */
+LB_API int lb_closure_step_targets(lb_ctx *pre, lb_ctx *post, const lb_mlp *mlp, float *T);
 /* Use the network in lb_step (NULL: plain RR). A cell whose standardised
  * prediction exceeds `bound` in magnitude, or whose corrected populations are
  * not all positive, takes the RR update instead and is counted. The network

@@ -62,6 +62,8 @@ SIGNATURES = {
     "lb_closure_features": (_i, [_vp, _vp, _vp]),
     "lb_closure_targets": (_i, [_vp, _vp, _vp]),
     "lb_coarsen": (_i, [_vp, _vp]),
+    "lb_coarsen_neq": (_i, [_vp, _vp, _d]),
+    "lb_closure_step_targets": (_i, [_vp, _vp, _vp, _vp]),
     "lb_set_closure": (_i, [_vp, _vp, ctypes.c_float]),
     "lb_closure_fallbacks": (_i, [_vp, ctypes.POINTER(_ll)]),
 }
@@ -241,9 +243,22 @@ class Solver:
                                           _ptr(rho_out), _ptr(u_out), _ptr(diag_out)))
 
     # -- learned closure (D3Q27, FP32 store, RR) ---------------------------
-    def coarsen_from(self, fine: "Solver"):
-        """2x2x2 box average of `fine`'s populations into this context."""
-        self._check(self._lib.lb_coarsen(fine.handle, self._h))
+    def coarsen_from(self, fine: "Solver", neq_scale: float | None = None):
+        """2x2x2 box average of `fine`'s populations into this context; with
+        neq_scale, the off-equilibrium part of each average scaled by it
+        (lb_coarsen_neq)."""
+        if neq_scale is None:
+            self._check(self._lib.lb_coarsen(fine.handle, self._h))
+        else:
+            self._check(self._lib.lb_coarsen_neq(fine.handle, self._h, float(neq_scale)))
+
+    def closure_step_targets(self, post: "Solver", mlp: "MLP"):
+        """Step-matching targets [N, 32] of this state against `post`
+        (lb_closure_step_targets)."""
+        import torch
+        T = torch.empty((self.n, MLP_OUT), device=self.device, dtype=torch.float32)
+        self._check(self._lib.lb_closure_step_targets(self._h, post.handle, mlp.handle, _ptr(T)))
+        return T
 
     def closure_features(self, mlp: "MLP"):
         import torch

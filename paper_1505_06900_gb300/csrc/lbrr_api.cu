@@ -795,10 +795,10 @@ int lb_closure_targets(lb_ctx *c, const lb_mlp *m, float *T) {
   return LB_OK;
 }
 
-int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
-  Range nvtx_range("lb_coarsen");
+static int coarsen(lb_ctx *fine, lb_ctx *coarse, double neq_scale) {
   LB_CHECK_CTX(fine);
   LB_CHECK_CTX(coarse);
+  if (!std::isfinite(neq_scale)) return fail(coarse, LB_EINVAL, "neq_scale must be finite");
   if (fine->lattice != LB_D3Q27 || coarse->lattice != LB_D3Q27 || fine->storage != LB_STORE_F32 ||
       coarse->storage != LB_STORE_F32 || fine->g.walls || coarse->g.walls)
     return fail(coarse, LB_EINVAL, "coarsening needs two periodic D3Q27 FP32 contexts");
@@ -811,10 +811,41 @@ int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
   if (fine->stream != coarse->stream) e = cudaStreamSynchronize(fine->stream);
   if (e == cudaSuccess)
     e = lbrr::launch_coarsen(fine->storage, fine->f, fine->g, fine->parity, coarse->storage,
-                             coarse->f, coarse->g, coarse->stream);
+                             coarse->f, coarse->g, coarse->stream, (float)neq_scale);
   if (e != cudaSuccess) return cuda_fail(coarse, e, "coarsen");
   coarse->parity = 0;
   coarse->steps = 0;
+  return LB_OK;
+}
+
+int lb_coarsen(lb_ctx *fine, lb_ctx *coarse) {
+  Range nvtx_range("lb_coarsen");
+  return coarsen(fine, coarse, 1.0);
+}
+
+int lb_coarsen_neq(lb_ctx *fine, lb_ctx *coarse, double neq_scale) {
+  Range nvtx_range("lb_coarsen_neq");
+  return coarsen(fine, coarse, neq_scale);
+}
+
+int lb_closure_step_targets(lb_ctx *pre, lb_ctx *post, const lb_mlp *m, float *T) {
+  LB_CHECK_CTX(pre);
+  LB_CHECK_CTX(post);
+  if (!m || !T) return fail(pre, LB_EINVAL, "null argument");
+  int rc = closure_capable(pre);
+  if (rc == LB_OK) rc = closure_capable(post);
+  if (rc != LB_OK) return rc;
+  if (pre->g.nx != post->g.nx || pre->g.ny != post->g.ny || pre->g.nz != post->g.nz ||
+      pre->device != post->device)
+    return fail(pre, LB_EINVAL, "the two states must share the grid and the device");
+  DeviceGuard dg(pre->device);
+  cudaError_t e = cudaSuccess;
+  if (post->stream != pre->stream) e = cudaStreamSynchronize(post->stream);
+  if (e == cudaSuccess)
+    e = lbrr::launch_step_targets(m->d, static_cast<const float *>(pre->f), pre->parity,
+                                  static_cast<const float *>(post->f), post->parity, pre->g,
+                                  (float)(1.0 - 1.0 / pre->tau), T, pre->stream);
+  if (e != cudaSuccess) return cuda_fail(pre, e, "closure step targets");
   return LB_OK;
 }
 

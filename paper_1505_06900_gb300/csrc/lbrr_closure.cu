@@ -77,6 +77,36 @@ __device__ __forceinline__ void ana1(float dm, float dz, float dp, float &e0, fl
   e2 = fmaf(2.0f / 3.0f, dm + dp, -dz / 3.0f);
 }
 
+// Hermite coefficients A[a][b][c] = sum_i H_a(xi_x) H_b(xi_y) H_c(xi_z) d_i of
+// a D3Q27 population vector (separable: x lines, then y, then z).
+__device__ __forceinline__ void hermite_analysis(const float (&d)[27], float (&A)[3][3][3]) {
+  float ax[3][9];  // [a][line (iy, iz)]
+#pragma unroll
+  for (int l = 0; l < 9; ++l) ana1(d[3 * l], d[3 * l + 1], d[3 * l + 2], ax[0][l], ax[1][l], ax[2][l]);
+  float axy[3][3][3];  // [a][b][iz]
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int iz = 0; iz < 3; ++iz)
+      ana1(ax[a][3 * iz], ax[a][3 * iz + 1], ax[a][3 * iz + 2], axy[a][0][iz], axy[a][1][iz],
+           axy[a][2][iz]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      ana1(axy[a][b][0], axy[a][b][1], axy[a][b][2], A[a][b][0], A[a][b][1], A[a][b][2]);
+}
+
+// Row `cell` of a target matrix: the order 3..6 coefficients of A divided by
+// div * out_scale, zero padded.
+__device__ __forceinline__ void write_targets(const MlpDevice &p, const float (&A)[3][3][3],
+                                              float div, float *__restrict__ row) {
+#pragma unroll
+  for (int k = 0; k < kMlpOutUsed; ++k)
+    row[k] = A[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] / (div * p.out_scale[k]);
+  for (int k = kMlpOutUsed; k < kMlpOut; ++k) row[k] = 0.f;
+}
+
 __global__ void __launch_bounds__(kAux)
     targets_kernel(MlpDevice p, const float *__restrict__ f, const Grid g, const int parity,
                    float *__restrict__ T) {
@@ -90,34 +120,53 @@ __global__ void __launch_bounds__(kAux)
   Lattice<27>::synth<0>(m, 1.0f, rr);  // f_RR - w (tau -> infinity)
 #pragma unroll
   for (int i = 0; i < 27; ++i) rr[i] = df[i] - rr[i];
-  float ax[3][9];  // [a][line (iy, iz)]
-#pragma unroll
-  for (int l = 0; l < 9; ++l) ana1(rr[3 * l], rr[3 * l + 1], rr[3 * l + 2], ax[0][l], ax[1][l], ax[2][l]);
-  float axy[3][3][3];  // [a][b][iz]
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int iz = 0; iz < 3; ++iz)
-      ana1(ax[a][3 * iz], ax[a][3 * iz + 1], ax[a][3 * iz + 2], axy[a][0][iz], axy[a][1][iz],
-           axy[a][2][iz]);
   float A[3][3][3];
+  hermite_analysis(rr, A);
+  write_targets(p, A, 1.0f, T + cell * kMlpOut);
+}
+
+// Step-matching targets of coarse cell x: P_i(x) = post_i(x + xi_i) (logical
+// populations; in the AA store, parity 0: slot i of x + xi_i, parity 1: slot
+// opp(i) of x itself), R = the RR post-collision of pre's cell x; the order
+// 3..6 coefficients of (P - R) / om1. Shifted values throughout: the weights
+// cancel in the difference.
+__global__ void __launch_bounds__(kAux)
+    step_targets_kernel(MlpDevice p, const float *__restrict__ fpre, const int ppre,
+                        const float *__restrict__ fpost, const int ppost, const Grid g,
+                        const float om1, float *__restrict__ T) {
+  const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
+  if (cell >= g.n) return;
+  int x, y, z;
+  cell_coords(cell, g, x, y, z);
+  float df[27], r[27];
+  load_logical<27, 0>(fpre, g, ppre, x, y, z, df);
+  const Macro m = Lattice<27>::moments(df);
+  Lattice<27>::synth<0>(m, om1, r);
+  const long long n = g.n;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      ana1(axy[a][b][0], axy[a][b][1], axy[a][b][2], A[a][b][0], A[a][b][1], A[a][b][2]);
-  float *row = T + cell * kMlpOut;
-#pragma unroll
-  for (int k = 0; k < kMlpOutUsed; ++k)
-    row[k] = A[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] / p.out_scale[k];
-  for (int k = kMlpOutUsed; k < kMlpOut; ++k) row[k] = 0.f;
+  for (int i = 0; i < 27; ++i) {
+    float pi;
+    if (ppost == 0) {
+      const long long dst = ((long long)wrap_add(z, vel(i, 2), g.nz) * g.ny +
+                             wrap_add(y, vel(i, 1), g.ny)) * g.nx + wrap_add(x, vel(i, 0), g.nx);
+      pi = __ldg(fpost + i * n + dst);
+    } else {
+      pi = __ldg(fpost + (26 - i) * n + cell);
+    }
+    r[i] = pi - r[i];
+  }
+  float A[3][3][3];
+  hermite_analysis(r, A);
+  write_targets(p, A, om1, T + cell * kMlpOut);
 }
 
 // -------------------------------------------------------------- coarsen --
-template <int SF, int SC>
+// RESCALE: the off-equilibrium part of the average is scaled,
+// f0(rho, u) + scale (fbar - f0(rho, u)) with rho, u the moments of fbar.
+template <int SF, int SC, bool RESCALE = false>
 __global__ void __launch_bounds__(kAux)
     coarsen_kernel(const typename Storage<SF>::T *__restrict__ ff, const Grid gf, const int parity,
-                   typename Storage<SC>::T *__restrict__ fc, const Grid gc) {
+                   typename Storage<SC>::T *__restrict__ fc, const Grid gc, const float scale) {
   const long long cell = (long long)blockIdx.x * kAux + threadIdx.x;
   if (cell >= gc.n) return;
   int x, y, z;
@@ -132,8 +181,16 @@ __global__ void __launch_bounds__(kAux)
     for (int i = 0; i < 27; ++i) acc[i] += df[i];
   }
 #pragma unroll
-  for (int i = 0; i < 27; ++i)
-    Storage<SC>::template store<27>(fc + i * gc.n + cell, i, 0.125f * acc[i]);
+  for (int i = 0; i < 27; ++i) acc[i] *= 0.125f;
+  if (RESCALE) {
+    const Macro m = Lattice<27>::moments(acc);
+    float eq[27];
+    Lattice<27>::synth<0>(m, 0.0f, eq);  // f0 - w
+#pragma unroll
+    for (int i = 0; i < 27; ++i) acc[i] = fmaf(scale, acc[i] - eq[i], eq[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 27; ++i) Storage<SC>::template store<27>(fc + i * gc.n + cell, i, acc[i]);
 }
 
 // ---------------------------------------------------------- closure step --
@@ -184,13 +241,24 @@ cudaError_t launch_targets(const MlpDevice &p, int storage, const void *f, const
 }
 
 cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int parity_f,
-                           int storage_c, void *fc, const Grid &gc, cudaStream_t st) {
+                           int storage_c, void *fc, const Grid &gc, cudaStream_t st,
+                           float neq_scale) {
   const unsigned nb = (unsigned)((gc.n + kAux - 1) / kAux);
-  if (storage_f == 0 && storage_c == 0)
+  if (storage_f != 0 || storage_c != 0) return cudaErrorInvalidValue;
+  if (neq_scale == 1.0f)
     coarsen_kernel<0, 0><<<nb, kAux, 0, st>>>(static_cast<const float *>(ff), gf, parity_f,
-                                              static_cast<float *>(fc), gc);
+                                              static_cast<float *>(fc), gc, 1.0f);
   else
-    return cudaErrorInvalidValue;
+    coarsen_kernel<0, 0, true><<<nb, kAux, 0, st>>>(static_cast<const float *>(ff), gf, parity_f,
+                                                    static_cast<float *>(fc), gc, neq_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_targets(const MlpDevice &p, const float *fpre, int ppre,
+                                const float *fpost, int ppost, const Grid &g, float om1, float *T,
+                                cudaStream_t st) {
+  step_targets_kernel<<<(unsigned)((g.n + kAux - 1) / kAux), kAux, 0, st>>>(p, fpre, ppre, fpost,
+                                                                           ppost, g, om1, T);
   return cudaGetLastError();
 }
 

@@ -144,9 +144,16 @@ cudaError_t launch_features(const MlpDevice &p, const float *mom, const Grid &g,
 // Standardised targets T [N][32] of the current populations.
 cudaError_t launch_targets(const MlpDevice &p, int storage, const void *f, const Grid &g,
                            int parity, float *T, cudaStream_t st);
-// 2x2x2 box average of a fine store into a coarse store (natural order).
+// 2x2x2 box average of a fine store into a coarse store (natural order),
+// the off-equilibrium part scaled by neq_scale (1: the plain average).
 cudaError_t launch_coarsen(int storage_f, const void *ff, const Grid &gf, int parity_f,
-                           int storage_c, void *fc, const Grid &gc, cudaStream_t st);
+                           int storage_c, void *fc, const Grid &gc, cudaStream_t st,
+                           float neq_scale = 1.0f);
+// Standardised step-matching targets T [N][32] of the coarse state fpre
+// against fpost (FP32 stores with their AA parities), om1 = 1 - 1/tau.
+cudaError_t launch_step_targets(const MlpDevice &p, const float *fpre, int ppre,
+                                const float *fpost, int ppost, const Grid &g, float om1, float *T,
+                                cudaStream_t st);
 // Network forward on the tcgen05 tensor cores (lbrr_mlp_tc.cu). With mom:
 // rows are the cells of grid *g, features from the moment field, outputs the
 // 17 standardised predictions Y [17][N]. Without: rows X [M][288] BF16, Y
