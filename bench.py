@@ -43,12 +43,12 @@ RATED_HBM_GBS = 7900.0   # nominal GB300 HBM3e bandwidth, beside the measured co
 # + dram__bytes_write.sum), keyed by the sha256 of the kernel sources it was
 # taken on; reported as null when the sources have changed since.
 # The 512^3 launch is too large for a multi-pass capture; the value is the
-# single-pass capture of the same kernel at 256^3 (mean of the even and odd
-# launches, 212.5 B per cell) scaled by the cell count, since the traffic
-# per cell does not depend on the grid size for this streaming kernel.
+# capture of the same kernel at 256^3 (mean of the even and odd launches,
+# 3,564,264,576 B, 212.45 B per cell) scaled by the cell count, since the
+# traffic per cell does not depend on the grid size for this streaming kernel.
 TRAFFIC = {
-    "d3q27_f32_512": {"kernel_sha": "f93afdb57dff9bb0", "bytes_per_launch": 28514870272,
-                      "source": "ncu 256^3 capture scaled to 512^3"},
+    "d3q27_f32_512": {"kernel_sha": "f93afdb57dff9bb0", "bytes_per_launch": 28514116608,
+                      "source": "ncu capture at 256^3 (mean of the even and odd launches) x 8"},
 }
 
 KERNEL_SOURCES = ["paper_1505_06900_gb300/csrc/lbrr_step.cu",
@@ -576,6 +576,7 @@ def run_gpu(args):
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": tr["source"] if traffic else None,
                      "kernel": "rr_step_kernel<27,f32,RR>", "peak_source": peak_src,
                      "frac_rated": achieved / RATED_HBM_GBS, "peak_rated": RATED_HBM_GBS,
                      "peak_rated_source": "nominal GB300 HBM3e bandwidth",

@@ -101,44 +101,42 @@ def generate_dataset(n_fine: int, mach: float, re: float, seeds, snapshots, frac
     fraction of the coarse cells at the snapshot fine steps of each seeded run,
     and the standardisation (in_mean, in_inv_std, out_scale).
 
-    Two passes over the (deterministic) fine runs: the first takes the
-    statistics from the coarse moment fields and the raw targets, the second
-    computes the features with the final standardisation."""
+    The feature standardisation comes from the first run's snapshots (a
+    phase shift only translates the periodic flow, so every run has the same
+    moment statistics); one pass over all runs then gathers features and raw
+    targets, and the targets are standardised at the end."""
     import torch
-    raw = B.MLP()  # identity standardisation
-    gen = torch.Generator(device="cuda").manual_seed(sample_seed)
-    picks, targs = {}, []
     s1 = torch.zeros(10, dtype=torch.float64, device="cuda")
     s2 = torch.zeros(10, dtype=torch.float64, device="cuda")
     cnt = 0
-    for si, ki, a, b in _snapshots(n_fine, mach, re, seeds, snapshots):
+    for _, _, a, _ in _snapshots(n_fine, mach, re, list(seeds)[:1], snapshots):
         rho, u, pi = a.moments()
         mom = torch.cat([(rho - 1.0).reshape(1, -1), u.reshape(3, -1), pi.reshape(6, -1)])
         mom = mom.double()
         s1 += mom.sum(1)
         s2 += (mom * mom).sum(1)
         cnt += mom.shape[1]
-        idx = torch.nonzero(torch.rand(a.n, device="cuda", generator=gen) < fraction)[:, 0]
-        picks[(si, ki)] = idx
-        targs.append(a.closure_step_targets(b, raw).index_select(0, idx))
-    raw.close()
+        del rho, u, pi, mom
     mean = s1 / cnt
     std = torch.sqrt(torch.clamp(s2 / cnt - mean * mean, min=0.0))
     # a moment kind that barely varies (e.g. a velocity component that stays
     # zero) must not turn round-off into large standardised features
     std = torch.maximum(std, 1e-3 * std.max())
+    mean_np = mean.cpu().numpy().astype(np.float32)
+    inv_np = (1.0 / std).cpu().numpy().astype(np.float32)
+    scaled = B.MLP()  # feature standardisation, raw targets (out_scale 1)
+    scaled.set_scaling(mean_np, inv_np, np.ones(17, np.float32))
+    gen = torch.Generator(device="cuda").manual_seed(sample_seed)
+    feats, targs = [], []
+    for _, _, a, b in _snapshots(n_fine, mach, re, seeds, snapshots):
+        idx = torch.nonzero(torch.rand(a.n, device="cuda", generator=gen) < fraction)[:, 0]
+        feats.append(a.closure_features(scaled).index_select(0, idx))
+        targs.append(a.closure_step_targets(b, scaled).index_select(0, idx))
+    scaled.close()
     T = torch.cat(targs)
     out_scale = T[:, :17].double().pow(2).mean(0).sqrt().clamp_min(1e-30)
     T[:, :17] = (T[:, :17].double() / out_scale).float()
-    mean_np = mean.cpu().numpy().astype(np.float32)
-    inv_np = (1.0 / std).cpu().numpy().astype(np.float32)
     out_np = out_scale.cpu().numpy().astype(np.float32)
-    scaled = B.MLP()
-    scaled.set_scaling(mean_np, inv_np, out_np)
-    feats = []
-    for si, ki, a, _ in _snapshots(n_fine, mach, re, seeds, snapshots):
-        feats.append(a.closure_features(scaled).index_select(0, picks[(si, ki)]))
-    scaled.close()
     return torch.cat(feats).contiguous(), T.contiguous(), (mean_np, inv_np, out_np)
 
 

@@ -75,13 +75,14 @@ def double_shear_2d_tau(n: int, mach: float = 0.1, re: float = 1000.0) -> float:
 
 
 def taylor_green_3d(n: int, mach: float = 0.1, phase=(0.0, 0.0, 0.0)):
-    """3D Taylor-Green vortex on [0, 2 pi)^3 sampled at cell centres."""
+    """3D Taylor-Green vortex on [0, 2 pi)^3 sampled at cell centres. The
+    factors of each axis are evaluated once on a 1-D array and broadcast."""
     u0 = mach * math.sqrt(CS2)
-    x, y, z = _grid(n, n, n)
     h = 2.0 * math.pi / n
-    X = (x + 0.5) * h + phase[0]
-    Y = (y + 0.5) * h + phase[1]
-    Z = (z + 0.5) * h + phase[2]
+    c = (np.arange(n, dtype=np.float64) + 0.5) * h
+    X = (c + phase[0])[None, None, :]
+    Y = (c + phase[1])[None, :, None]
+    Z = (c + phase[2])[:, None, None]
     ux = u0 * np.sin(X) * np.cos(Y) * np.cos(Z)
     uy = -u0 * np.cos(X) * np.sin(Y) * np.cos(Z)
     uz = np.zeros_like(ux)
