@@ -33,7 +33,10 @@ the learned-closure extension built around the RR step:
   bias-corrected);
 * the corrected collision: the predicted 17 coefficients (unstandardised) are
   added to the recursion's off-equilibrium coefficients before the
-  (1 - 1/tau) relaxation (oracle C function ora_collide_cell_closure).
+  (1 - 1/tau) relaxation (oracle C function ora_collide_cell_closure);
+  with a dead zone theta >= 0, each standardised prediction y is first shrunk
+  to sign(y) max(|y| - theta, 0), so that predictions at the level of the
+  network's own error leave the cell to plain RR.
 
 All arithmetic is numpy float64 except the collisions, which call the C
 oracle.
@@ -196,21 +199,25 @@ def targets(f: np.ndarray) -> np.ndarray:
 
 
 def predict_delta(X: np.ndarray, p: dict, out_scale: np.ndarray,
-                  bf16: bool = False) -> np.ndarray:
+                  bf16: bool = False, dead_zone: float = 0.0) -> np.ndarray:
     """Unstandardised correction [N, 17] predicted by the network (bf16: with
-    the features and hidden layers rounded to bfloat16)."""
+    the features and hidden layers rounded to bfloat16), each standardised
+    prediction shrunk by the dead zone first."""
     Y, _ = forward(bf16_round(X) if bf16 else X, p, round_hidden=bf16)
-    return Y[:, :N_OUT_USED] * out_scale
+    Y = Y[:, :N_OUT_USED]
+    Y = np.sign(Y) * np.maximum(np.abs(Y) - dead_zone, 0.0)
+    return Y * out_scale
 
 
 def step_closure(f: np.ndarray, tau: float, p: dict, mean, inv_std, out_scale,
-                 bf16: bool = False) -> np.ndarray:
+                 bf16: bool = False, dead_zone: float = 0.0) -> np.ndarray:
     """One update of the D3Q27 RR scheme with the learned correction: features
     from the pre-collision moments, corrected collision of every cell, periodic
     streaming (pull)."""
     from . import lattice_tables
     q, nz, ny, nx = f.shape
-    delta = predict_delta(features(moment_field(f), mean, inv_std), p, out_scale, bf16)
+    delta = predict_delta(features(moment_field(f), mean, inv_std), p, out_scale, bf16,
+                          dead_zone)
     post = np.empty_like(f).reshape(q, -1)
     ff = f.reshape(q, -1)
     for c in range(nx * ny * nz):

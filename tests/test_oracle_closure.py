@@ -246,3 +246,27 @@ def test_coarsen_neq_scale_matches_the_constitutive_relation_on_the_coarse_grid(
             assert err < tol, err
         else:
             assert err > 0.3, err
+
+
+def test_closure_step_dead_zone():
+    """A dead zone at least as wide as every standardised prediction leaves
+    plain RR (the oracle's own collide-and-stream); none leaves the plain
+    closure step; in between, the correction of a prediction y is the one of
+    sign(y)(|y| - theta), continuous in theta."""
+    shape, tau = (4, 3, 3), 0.6
+    rng = np.random.default_rng(14)
+    f = _random_state(shape, 15, amp=0.01)
+    p = C.unpack(0.05 * rng.standard_normal(C.N_PARAMS))
+    mean, inv = np.zeros(10), np.full(10, 30.0)
+    out_scale = np.full(17, 1e-3)
+    X = C.features(C.moment_field(f), mean, inv)
+    ymax = np.abs(C.forward(X, p)[0][:, :17]).max()
+    wide = C.step_closure(f, tau, p, mean, inv, out_scale, dead_zone=ymax * 1.01)
+    assert np.abs(wide - O.step(O.D3Q27, shape, tau, f, 1)).max() < 1e-15
+    none = C.step_closure(f, tau, p, mean, inv, out_scale, dead_zone=0.0)
+    plain = C.step_closure(f, tau, p, mean, inv, out_scale)
+    assert np.array_equal(none, plain)
+    a = C.step_closure(f, tau, p, mean, inv, out_scale, dead_zone=0.3 * ymax)
+    b = C.step_closure(f, tau, p, mean, inv, out_scale, dead_zone=0.3 * ymax + 1e-7)
+    assert np.abs(a - b).max() < 1e-8
+    assert np.abs(a - plain).max() > 1e-6 and np.abs(a - wide).max() > 1e-6
