@@ -225,7 +225,8 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- GPU arm --
 def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_every, stream,
-                 sync_all, sampler=None, u_at=None, closure=None, lattice=None):
+                 sync_all, sampler=None, u_at=None, closure=None, lattice=None,
+                 dead_zone=0.0):
     """Warm up, then time `steps` updates with the diagnostics reduction every
     `diag_every` updates inside the timed region; returns timing and per-launch
     data. With u_at, the run then continues (untimed) to u_at updates in all
@@ -236,7 +237,7 @@ def time_variant(B, torch, n, storage, steps, warmup, tau, rho_d, u_d, diag_ever
         s.init_fields(rho_d, u_d)
         diag0 = s.diagnostics()
         if closure is not None:
-            s.set_closure(closure)
+            s.set_closure(closure, dead_zone=dead_zone)
         s.step(warmup)
         for _ in range(max(1, warmup // diag_every)):
             s.diagnostics()
@@ -326,7 +327,8 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
     u_d = torch.from_numpy(u.astype(np.float32)).cuda()
     diag_every = min(DIAG_EVERY, steps)
     ml = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
-                      diag_every, stream, sync_all, sampler, closure=net)
+                      diag_every, stream, sync_all, sampler, closure=net,
+                      dead_zone=CL.DEAD_ZONE)
     rr = time_variant(B, torch, n_coarse, B.STORE_F32, steps, warmup, tau_c, rho_d, u_d,
                       diag_every, stream, sync_all, sampler)
     cells = n_coarse ** 3
@@ -357,7 +359,8 @@ def learned_variant(B, torch, n_coarse, steps, warmup, stream, sync_all, fine_ms
                        f"closure) relative L2 of u",
         "training": {"samples": rep["samples"], "loss_first": rep["loss_first"],
                      "loss_last": rep["loss_last"], "seconds": train_s,
-                     "gain": rep["gain"], "fallbacks_in_evaluation": rep["fallbacks"]},
+                     "gain": rep["gain"], "dead_zone": rep["dead_zone"],
+                     "fallbacks_in_evaluation": rep["fallbacks"]},
     }
 
 

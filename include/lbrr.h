@@ -309,6 +309,12 @@ LB_API int lb_closure_step_targets(lb_ctx *pre, lb_ctx *post, const lb_mlp *mlp,
  * expires (reported as LB_ETIMEOUT), part of the cells of that update were
  * not updated: re-initialise or restore a checkpoint. */
 LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
+/* The same with a dead zone (extension, not in the paper): each standardised
+ * prediction y is shrunk to sign(y) max(|y| - dead_zone, 0) before it scales
+ * its coefficient, so that predictions at the level of the network's own
+ * error leave the cell to plain RR (dead_zone finite and >= 0; 0 is
+ * lb_set_closure). The bound applies to the unshrunk prediction. */
+LB_API int lb_set_closure_ex(lb_ctx *ctx, const lb_mlp *mlp, float bound, float dead_zone);
 /* Cells that fell back to RR since the closure was first set (host out).
  * Synchronises; LB_ETIMEOUT if a bounded tensor-core wait of the closure's
  * network ever expired in lb_step. */

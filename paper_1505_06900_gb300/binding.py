@@ -63,6 +63,7 @@ SIGNATURES = {
     "lb_closure_targets": (_i, [_vp, _vp, _vp]),
     "lb_coarsen": (_i, [_vp, _vp]),
     "lb_coarsen_neq": (_i, [_vp, _vp, _d]),
+    "lb_set_closure_ex": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
     "lb_closure_step_targets": (_i, [_vp, _vp, _vp, _vp]),
     "lb_set_closure": (_i, [_vp, _vp, ctypes.c_float]),
     "lb_closure_fallbacks": (_i, [_vp, ctypes.POINTER(_ll)]),
@@ -272,8 +273,11 @@ class Solver:
         self._check(self._lib.lb_closure_targets(self._h, mlp.handle, _ptr(T)))
         return T
 
-    def set_closure(self, mlp, bound: float = 8.0):
-        self._check(self._lib.lb_set_closure(self._h, mlp.handle if mlp else None, float(bound)))
+    def set_closure(self, mlp, bound: float = 8.0, dead_zone: float = 0.0):
+        """Learned closure for the following updates (None: plain RR); the
+        dead zone shrinks each standardised prediction (lb_set_closure_ex)."""
+        self._check(self._lib.lb_set_closure_ex(self._h, mlp.handle if mlp else None,
+                                                float(bound), float(dead_zone)))
         self._closure = mlp
 
     def set_wait_limit(self, iterations: int):

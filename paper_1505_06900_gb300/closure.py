@@ -25,7 +25,10 @@ Recipe (step-matching targets on filtered fine data):
   * Adam on minibatches with a cosine-decaying learning rate;
   * the coarse run adds GAIN times the predicted correction: the orders 0 and
     1 of B are out of a local collision's reach, and correcting orders 3..6 in
-    full against them overshoots;
+    full against them overshoots; each standardised prediction is shrunk by
+    the dead zone DEAD_ZONE first (sign(y) max(|y| - DEAD_ZONE, 0)), so that
+    where the coarse grid still resolves the flow and the correction is below
+    the network's own error, the cell keeps plain RR;
   * evaluation on a held-out phase: the coarse run (tau_c, one coarse step
     per two fine steps) with and without the closure, both started from the
     filtered fine state, against the filtered fine run.
@@ -41,6 +44,7 @@ from . import workloads as W
 
 
 GAIN = 0.5  # share of the predicted correction the coarse run applies
+DEAD_ZONE = 0.25  # shrinkage of the standardised predictions (lb_set_closure_ex)
 
 
 def coarse_tau(tau_f: float) -> float:
@@ -184,7 +188,7 @@ def inference_net(params, scaling, gain: float = GAIN) -> B.MLP:
 
 
 def evaluate(net, n_fine: int, mach: float, re: float, seed: int, coarse_steps: int,
-             bound: float = 8.0, every: int | None = None):
+             bound: float = 8.0, every: int | None = None, dead_zone: float = DEAD_ZONE):
     """Relative L2 errors of u of the coarse RR run and of the coarse run with
     the closure against the filtered fine run, after coarse_steps coarse steps
     (and every `every` coarse steps on the way, in "history")."""
@@ -197,7 +201,7 @@ def evaluate(net, n_fine: int, mach: float, re: float, seed: int, coarse_steps: 
     ml = B.Solver(B.D3Q27, (nc, nc, nc), tc)
     rr.coarsen_from(fine, scale)
     ml.coarsen_from(fine, scale)
-    ml.set_closure(net, bound)
+    ml.set_closure(net, bound, dead_zone)
     hist = []
     done = 0
     every = every or coarse_steps
@@ -244,7 +248,7 @@ def held_out_loss(net, n_fine: int, mach: float, re: float, seed: int, snapshots
 
 def study(n_fine=64, mach=0.3, re=1600.0, train_seeds=range(1, 9), eval_seed=9,
           snapshots=None, fraction=0.25, steps=3000, batch=8192, lr=2e-3, coarse_steps=200,
-          gain=GAIN, every=None):
+          gain=GAIN, every=None, dead_zone=DEAD_ZONE):
     """The whole recipe at one size; returns the network the coarse run uses
     (output scale times the gain), the training standardisation and a report.
     Snapshots default to every 24 fine steps over the evaluated interval."""
@@ -259,8 +263,10 @@ def study(n_fine=64, mach=0.3, re=1600.0, train_seeds=range(1, 9), eval_seed=9,
     trainer.close()
     report = {"samples": samples, "loss_first": losses[0][1],
               "loss_last": losses[-1][1], "n_fine": n_fine, "mach": mach, "re": re,
-              "gain": gain, "snapshots": [snapshots[0], snapshots[-1], len(snapshots)]}
-    report.update(evaluate(net, n_fine, mach, re, eval_seed, coarse_steps, every=every))
+              "gain": gain, "dead_zone": dead_zone,
+              "snapshots": [snapshots[0], snapshots[-1], len(snapshots)]}
+    report.update(evaluate(net, n_fine, mach, re, eval_seed, coarse_steps, every=every,
+                           dead_zone=dead_zone))
     return net, scaling, report
 
 
@@ -284,12 +290,13 @@ def main():
     ap.add_argument("--snapshots", type=int, nargs="+",
                     help="fine steps of the training snapshots (default: every 24 over the run)")
     ap.add_argument("--gain", type=float, default=GAIN)
+    ap.add_argument("--dead-zone", type=float, default=DEAD_ZONE)
     args = ap.parse_args()
     t0 = time.perf_counter()
     net, scaling, rep = study(n_fine=args.n_fine, fraction=args.fraction, steps=args.steps,
                               coarse_steps=args.coarse_steps, every=args.every,
                               snapshots=tuple(args.snapshots) if args.snapshots else None,
-                              gain=args.gain)
+                              gain=args.gain, dead_zone=args.dead_zone)
     rep["seconds_study"] = time.perf_counter() - t0
     snaps = tuple(args.snapshots) if args.snapshots else dense_snapshots(2 * args.coarse_steps, 96)
     rep["held_out_a_priori"] = held_out_loss(net, args.n_fine, rep["mach"], rep["re"], 9, snaps,

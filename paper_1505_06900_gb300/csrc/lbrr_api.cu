@@ -36,6 +36,7 @@ struct lb_ctx {
   CUtensorMap xs_map{};        // its tensor map
   const lb_mlp *closure = nullptr;  // learned closure in use (not owned)
   float closure_bound = 0.f;
+  float closure_dead_zone = 0.f;
   unsigned long long *fallbacks = nullptr;  // device counter of cells that fell back to RR
   cudaStream_t stream = nullptr;
   // CUDA graphs of kGraphSteps plain updates starting at parity 0 / 1 (built
@@ -363,6 +364,7 @@ int lb_step(lb_ctx *c, int n) {
       if (e == cudaSuccess)
         e = lbrr::launch_mlp_conv_step(c->closure->d, c->xs_map, c->g, static_cast<float *>(c->f),
                                        om1, c->parity, c->fallbacks, c->closure_bound,
+                                       c->closure_dead_zone,
                                        c->closure->status, c->closure->nblocks, c->stream);
     } else if (c->closure) {
       e = lbrr::launch_moment_field(c->storage, c->f, c->g, c->parity, c->mom, c->stream);
@@ -372,6 +374,7 @@ int lb_step(lb_ctx *c, int n) {
       if (e == cudaSuccess)
         e = lbrr::launch_step_delta(c->closure->d, static_cast<float *>(c->f), c->g, om1,
                                     c->parity, c->ystd, c->fallbacks, c->closure_bound,
+                                    c->closure_dead_zone,
                                     c->stream);
     } else {
       e = lbrr::launch_step(c->q, c->storage, c->collision, c->f, c->g, om1, c->parity,
@@ -849,13 +852,15 @@ int lb_closure_step_targets(lb_ctx *pre, lb_ctx *post, const lb_mlp *m, float *T
   return LB_OK;
 }
 
-int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
+int lb_set_closure_ex(lb_ctx *c, const lb_mlp *m, float bound, float dead_zone) {
   LB_CHECK_CTX(c);
   if (!m) {
     c->closure = nullptr;
     return LB_OK;
   }
   if (!(bound > 0.f)) return fail(c, LB_EINVAL, "bound must be positive");
+  if (!(dead_zone >= 0.f) || !std::isfinite(dead_zone))
+    return fail(c, LB_EINVAL, "dead_zone must be a finite number >= 0");
   int rc = closure_capable(c);
   if (rc == LB_OK) rc = ensure_mom(c, true);
   if (rc != LB_OK) return rc;
@@ -870,7 +875,12 @@ int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
   }
   c->closure = m;
   c->closure_bound = bound;
+  c->closure_dead_zone = dead_zone;
   return LB_OK;
+}
+
+int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
+  return lb_set_closure_ex(c, m, bound, 0.f);
 }
 
 int lb_closure_fallbacks(lb_ctx *c, long long *count) {

@@ -204,7 +204,7 @@ template <int PARITY>
 __global__ void __launch_bounds__(kDT)
     rr_step_delta_kernel(MlpDevice p, float *__restrict__ f, const Grid g, const float om1,
                          const float *__restrict__ ystd, unsigned long long *fallbacks,
-                         const float bound) {
+                         const float bound, const float dead_zone) {
   const int x = blockIdx.x * kDT + threadIdx.x;
   if (x >= g.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(kDT)
   float yk[kMlpOutUsed];
 #pragma unroll
   for (int k = 0; k < kMlpOutUsed; ++k) yk[k] = __ldg(ystd + k * g.n + cell);
-  closure_update_cell<PARITY>(p, f, g, om1, x, y, z, yk, fallbacks, bound);
+  closure_update_cell<PARITY>(p, f, g, om1, x, y, z, yk, fallbacks, bound, dead_zone);
 }
 
 }  // namespace
@@ -264,12 +264,14 @@ cudaError_t launch_step_targets(const MlpDevice &p, const float *fpre, int ppre,
 
 cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
                               const float *ystd, unsigned long long *fallbacks, float bound,
-                              cudaStream_t st) {
+                              float dead_zone, cudaStream_t st) {
   const dim3 grid((g.nx + kDT - 1) / kDT, g.ny, g.nz);
   if (parity == 0)
-    rr_step_delta_kernel<0><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound);
+    rr_step_delta_kernel<0><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound,
+                                                 dead_zone);
   else
-    rr_step_delta_kernel<1><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound);
+    rr_step_delta_kernel<1><<<grid, kDT, 0, st>>>(p, f, g, om1, ystd, fallbacks, bound,
+                                                 dead_zone);
   return cudaGetLastError();
 }
 

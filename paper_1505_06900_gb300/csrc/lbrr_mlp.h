@@ -56,17 +56,18 @@ __host__ __device__ constexpr int hi_pow(int k, int axis) {
 
 // The closure update of cell (x, y, z) of an FP32 D3Q27 AA store (parity as
 // in lbrr_step.cu): the RR coefficients plus (1 - 1/tau) times the network's
-// correction, ystd[k] out_scale[k] added to coefficient k of orders 3..6;
-// plain RR for the cell (counted in *fallbacks) when a standardised
-// prediction exceeds the bound (or is not a number) or a corrected population
-// is not positive. Each cell reads exactly the locations it writes. IDX is
+// correction, y'[k] out_scale[k] added to coefficient k of orders 3..6, with
+// y' = sign(y) max(|y| - dead_zone, 0) the standardised prediction y = ystd[k]
+// shrunk by the dead zone; plain RR for the cell (counted in *fallbacks) when a
+// standardised prediction exceeds the bound (or is not a number) or a
+// corrected population is not positive. Each cell reads exactly the locations it writes. IDX is
 // the type of the element offsets: int needs 27 N < 2^31 (fewer registers).
 template <int PARITY, typename IDX = long long>
 __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *__restrict__ f,
                                                     const Grid &g, const float om1, int x, int y,
                                                     int z, const float (&ystd)[kMlpOutUsed],
                                                     unsigned long long *fallbacks,
-                                                    const float bound) {
+                                                    const float bound, const float dead_zone) {
   const IDX n = (IDX)g.n;
   const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
   const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
@@ -91,7 +92,8 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
   for (int k = 0; k < kMlpOutUsed; ++k) {
     const float yk = ystd[k];
     use = use && (fabsf(yk) <= bound);  // also false for NaN
-    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yk * p.out_scale[k]);
+    const float yd = copysignf(fmaxf(fabsf(yk) - dead_zone, 0.0f), yk);
+    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yd * p.out_scale[k]);
   }
   float out[27];
   if (use) {
@@ -179,11 +181,12 @@ cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid
 // not been updated.
 cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
                                  float *f, float om1, int parity, unsigned long long *fallbacks,
-                                 float bound, int *status, int nblocks, cudaStream_t st);
+                                 float bound, float dead_zone, int *status, int nblocks,
+                                 cudaStream_t st);
 // One update of an FP32 D3Q27 store with the learned correction: ystd [17][N]
 // holds the network's standardised predictions for the current populations.
 cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,
                               const float *ystd, unsigned long long *fallbacks, float bound,
-                              cudaStream_t st);
+                              float dead_zone, cudaStream_t st);
 
 }  // namespace lbrr

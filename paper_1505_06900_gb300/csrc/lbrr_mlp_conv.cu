@@ -152,7 +152,7 @@ template <int PARITY, typename IDX>
 __global__ void __launch_bounds__(kConvThreads, 1)
     mlp_conv_kernel(MlpDevice p, const __grid_constant__ CUtensorMap xs_map, const Grid g,
                     float *__restrict__ f, const float om1, unsigned long long *fallbacks,
-                    const float bound, int *status) {
+                    const float bound, const float dead_zone, int *status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
@@ -362,7 +362,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       const uint32_t row = t / tpr;
       const int x = (int)(t - row * tpr) * kCRows + r;
       closure_update_cell<PARITY, IDX>(p, f, g, om1, x, (int)(row % (uint32_t)g.ny),
-                                       (int)(row / (uint32_t)g.ny), yk, fallbacks, bound);
+                                       (int)(row / (uint32_t)g.ny), yk, fallbacks, bound,
+                                       dead_zone);
     }
   }
 
@@ -457,7 +458,8 @@ cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid
 
 cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
                                  float *f, float om1, int parity, unsigned long long *fallbacks,
-                                 float bound, int *status, int nblocks, cudaStream_t st) {
+                                 float bound, float dead_zone, int *status, int nblocks,
+                                 cudaStream_t st) {
   // 32-bit element offsets where every slot of the store is addressable so
   auto kern = 27 * g.n < (1LL << 31) ? (parity ? mlp_conv_kernel<1, int> : mlp_conv_kernel<0, int>)
                                      : (parity ? mlp_conv_kernel<1, long long>
@@ -469,7 +471,8 @@ cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, con
   if (tiles >= (1LL << 31)) return cudaErrorInvalidValue;
   const int nb = (int)(tiles < nblocks ? tiles : nblocks);
   if (nb < 1) return cudaSuccess;
-  kern<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, f, om1, fallbacks, bound, status);
+  kern<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, f, om1, fallbacks, bound, dead_zone,
+                                            status);
   return cudaGetLastError();
 }
 

@@ -413,6 +413,42 @@ def test_closure_step_matches_oracle_and_zero_network_is_rr(shape):
         assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
 
 
+def test_closure_step_with_a_dead_zone_matches_oracle():
+    """Two closure updates with the standardised predictions shrunk by a dead
+    zone, against the reference at the kernels' precision; a dead zone wider
+    than every prediction is plain RR bit for bit."""
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(61, 2e-5, (128, 3, 3))
+    net = B.MLP(C.pack(p))
+    net.set_scaling(mean, inv, out_scale)
+    theta = 0.4
+    with B.Solver(B.D3Q27, shape, tau) as s:
+        s.set_populations(torch.from_numpy(df).cuda())
+        s.set_closure(net, bound=1e6, dead_zone=theta)
+        s.step(2)
+        got = s.populations().cpu().numpy()
+    f = f64_state(O.D3Q27, df)
+    m64, i64, o64 = (np.asarray(v, np.float32).astype(np.float64) for v in (mean, inv, out_scale))
+    plain = f.copy()
+    for _ in range(2):
+        f = C.step_closure(f, tau, p, m64, i64, o64, bf16=True, dead_zone=theta)
+        plain = C.step_closure(plain, tau, p, m64, i64, o64, bf16=True)
+    rr = O.step(O.D3Q27, shape, tau, f64_state(O.D3Q27, df), 2)
+    effect = max_rel_to_weight(O.D3Q27, shifted(O.D3Q27, rr), shifted(O.D3Q27, f))
+    assert effect > 1e-4
+    # the dead zone changes the update by far more than the tolerance
+    assert max_rel_to_weight(O.D3Q27, shifted(O.D3Q27, plain), shifted(O.D3Q27, f)) > 10 * (
+        1e-6 + 1e-2 * effect)
+    assert max_rel_to_weight(O.D3Q27, got, shifted(O.D3Q27, f)) <= 1e-6 + 1e-2 * effect
+    with B.Solver(B.D3Q27, shape, tau) as a, B.Solver(B.D3Q27, shape, tau) as b:
+        a.set_populations(torch.from_numpy(df).cuda())
+        b.set_populations(torch.from_numpy(df).cuda())
+        a.set_closure(net, bound=1e6, dead_zone=1e6)
+        a.step(3)
+        b.step(3)
+        assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
+    net.close()
+
+
 def test_closure_fallback_to_rr():
     """A bound below every prediction sends every cell to the RR update, and
     each such cell update is counted."""
@@ -435,7 +471,8 @@ def test_trained_closure_gain_on_a_held_out_phase():
     on the recipe at fine 64^3 -> coarse 32^3 (Ma 0.3, Re 1600, eight seeded
     training phases, the ninth held out; step-matching targets on filtered
     states whose off-equilibrium part is rescaled by 2 tau_c / tau_f; the
-    correction applied at half strength).
+    correction applied at half strength, each standardised prediction shrunk
+    by the recipe's dead zone).
 
     A priori, on the held-out phase's filtered snapshots, it predicts most of
     the order 3..6 correction that would make a coarse RR update reproduce two
@@ -455,4 +492,20 @@ def test_trained_closure_gain_on_a_held_out_phase():
     for steps, err_rr, err_closure in rep["history"]:
         assert err_closure < err_rr, (steps, err_rr, err_closure)
     assert rep["fallbacks"] < 0.05 * rep["cells"] * rep["coarse_steps"]
+    net.close()
+
+
+def test_trained_closure_never_worse_than_rr_at_128():
+    """The same recipe at fine 128^3 -> coarse 64^3 over 400 coarse steps
+    (t = 6.8): while the coarse grid resolves the vortex the dead zone leaves
+    the run at coarse RR's error (to 1e-6 of it), and once it under-resolves
+    the flow (t > 3) the closure run ends at least 5% closer to the filtered
+    fine run than coarse RR."""
+    from paper_1505_06900_gb300 import closure as CL
+    net, _, rep = CL.study(n_fine=128, steps=3000, coarse_steps=400, fraction=0.05, every=100)
+    print(f"u error (coarse steps, rr, closure): {rep['history']}; fallbacks {rep['fallbacks']}")
+    for steps, err_rr, err_closure in rep["history"]:
+        assert err_closure <= err_rr * (1 + 1e-6), (steps, err_rr, err_closure)
+    for steps, err_rr, err_closure in rep["history"][2:]:
+        assert err_closure < 0.95 * err_rr, (steps, err_rr, err_closure)
     net.close()
