@@ -93,6 +93,16 @@ def test_null_context_is_rejected(lib):
     lib.lb_destroy(None)
 
 
+def test_closure_entry_points_reject_null_handles(lib):
+    """The learned-closure and inspection entry points validate their handles
+    and buffers before any device work."""
+    assert lib.lb_coarsen_neq(None, None, 2.0) == B.LB_EINVAL
+    assert lib.lb_closure_step_targets(None, None, None, None) == B.LB_EINVAL
+    assert lib.lb_set_closure_ex(None, None, 8.0, 0.25) == B.LB_EINVAL
+    assert lib.lb_mlp_forward_trace(None, None, 1, None, None) == B.LB_EINVAL
+    assert lib.lb_mlp_gradients_trace(None, None, None, 1, None, None, None) == B.LB_EINVAL
+
+
 def test_product_path_does_not_use_the_oracle():
     """The CUDA package never imports, links or runs anything under oracle/."""
     pkg = os.path.join(ROOT, "paper_1505_06900_gb300")
