@@ -413,11 +413,14 @@ def test_closure_step_matches_oracle_and_zero_network_is_rr(shape):
         assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
 
 
-def test_closure_step_with_a_dead_zone_matches_oracle():
+# (128, 3, 3): the fused row-tile network; (80, 3, 4): predictions through
+# device memory to the separate update kernel
+@pytest.mark.parametrize("shape", [(128, 3, 3), (80, 3, 4)])
+def test_closure_step_with_a_dead_zone_matches_oracle(shape):
     """Two closure updates with the standardised predictions shrunk by a dead
     zone, against the reference at the kernels' precision; a dead zone wider
     than every prediction is plain RR bit for bit."""
-    shape, tau, df, p, mean, inv, out_scale = _closure_case(61, 2e-5, (128, 3, 3))
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(61, 2e-5, shape)
     net = B.MLP(C.pack(p))
     net.set_scaling(mean, inv, out_scale)
     theta = 0.4
