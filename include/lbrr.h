@@ -315,6 +315,18 @@ LB_API int lb_set_closure(lb_ctx *ctx, const lb_mlp *mlp, float bound);
  * error leave the cell to plain RR (dead_zone finite and >= 0; 0 is
  * lb_set_closure). The bound applies to the unshrunk prediction. */
 LB_API int lb_set_closure_ex(lb_ctx *ctx, const lb_mlp *mlp, float bound, float dead_zone);
+/* Inspection form of one closure update (no counterpart in the paper; it lets
+ * a test check the fused kernel's network layer by layer): on a context whose
+ * learned closure runs the fused row-tile kernel (nx a multiple of 128), one
+ * update exactly as lb_step(ctx, 1) performs it, that also writes
+ *   trace [N][145] (device, FP32, cells in x-fastest order): the activations
+ *     of layers 1 (0..63) and 2 (64..127) before their BF16 rounding and the
+ *     17 standardised predictions (128..144) of every cell;
+ *   xs_out (device, (nx+2)(ny+2)(nz+2) x 16 BF16): the standardised moments
+ *     the update's network read, channels-last with a one-cell periodic halo,
+ *     channels 0..9 = rho - 1, u, Pi1 (xx, xy, xz, yy, yz, zz), 10..15 zero.
+ * LB_EINVAL on other contexts. */
+LB_API int lb_closure_step_trace(lb_ctx *ctx, float *trace, void *xs_out);
 /* Cells that fell back to RR since the closure was first set (host out).
  * Synchronises; LB_ETIMEOUT if a bounded tensor-core wait of the closure's
  * network ever expired in lb_step. */

@@ -214,10 +214,16 @@ def step_closure(f: np.ndarray, tau: float, p: dict, mean, inv_std, out_scale,
     """One update of the D3Q27 RR scheme with the learned correction: features
     from the pre-collision moments, corrected collision of every cell, periodic
     streaming (pull)."""
-    from . import lattice_tables
-    q, nz, ny, nx = f.shape
     delta = predict_delta(features(moment_field(f), mean, inv_std), p, out_scale, bf16,
                           dead_zone)
+    return step_with_delta(f, tau, delta)
+
+
+def step_with_delta(f: np.ndarray, tau: float, delta: np.ndarray) -> np.ndarray:
+    """One update with given unstandardised corrections delta [N, 17]: the
+    corrected collision of every cell, then periodic streaming (pull)."""
+    from . import lattice_tables
+    q, nz, ny, nx = f.shape
     post = np.empty_like(f).reshape(q, -1)
     ff = f.reshape(q, -1)
     for c in range(nx * ny * nz):

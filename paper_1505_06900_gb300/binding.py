@@ -64,6 +64,7 @@ SIGNATURES = {
     "lb_coarsen": (_i, [_vp, _vp]),
     "lb_coarsen_neq": (_i, [_vp, _vp, _d]),
     "lb_set_closure_ex": (_i, [_vp, _vp, ctypes.c_float, ctypes.c_float]),
+    "lb_closure_step_trace": (_i, [_vp, _vp, _vp]),
     "lb_closure_step_targets": (_i, [_vp, _vp, _vp, _vp]),
     "lb_set_closure": (_i, [_vp, _vp, ctypes.c_float]),
     "lb_closure_fallbacks": (_i, [_vp, ctypes.POINTER(_ll)]),
@@ -272,6 +273,16 @@ class Solver:
         T = torch.empty((self.n, MLP_OUT), device=self.device, dtype=torch.float32)
         self._check(self._lib.lb_closure_targets(self._h, mlp.handle, _ptr(T)))
         return T
+
+    def closure_step_trace(self):
+        """One closure update with its inspection outputs (lb_closure_step_trace):
+        trace [N, 145] FP32 and the feature source [nz+2, ny+2, nx+2, 16] BF16."""
+        import torch
+        tr = torch.empty((self.n, 145), device=self.device, dtype=torch.float32)
+        xs = torch.empty((self.nz + 2, self.ny + 2, self.nx + 2, 16), device=self.device,
+                         dtype=torch.bfloat16)
+        self._check(self._lib.lb_closure_step_trace(self._h, _ptr(tr), _ptr(xs)))
+        return tr, xs
 
     def set_closure(self, mlp, bound: float = 8.0, dead_zone: float = 0.0):
         """Learned closure for the following updates (None: plain RR); the

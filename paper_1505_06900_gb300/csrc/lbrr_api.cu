@@ -883,6 +883,30 @@ int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
   return lb_set_closure_ex(c, m, bound, 0.f);
 }
 
+int lb_closure_step_trace(lb_ctx *c, float *trace, void *xs_out) {
+  LB_CHECK_CTX(c);
+  if (!trace || !xs_out) return fail(c, LB_EINVAL, "null trace or feature-source buffer");
+  if (!c->closure || !c->xs)
+    return fail(c, LB_EINVAL,
+                "needs a learned closure on a grid of whole 128-cell row tiles (lb_set_closure)");
+  DeviceGuard dg(c->device);
+  const float om1 = (float)(1.0 - 1.0 / c->tau);
+  cudaError_t e = lbrr::launch_feature_source(c->closure->d, static_cast<const float *>(c->f),
+                                              c->g, c->parity, c->xs, c->stream);
+  if (e == cudaSuccess)
+    e = lbrr::launch_mlp_conv_step(c->closure->d, c->xs_map, c->g, static_cast<float *>(c->f),
+                                   om1, c->parity, c->fallbacks, c->closure_bound,
+                                   c->closure_dead_zone, c->closure->status,
+                                   c->closure->nblocks, c->stream, trace);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(xs_out, c->xs, lbrr::feature_source_bytes(c->g), cudaMemcpyDeviceToDevice,
+                        c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "closure step trace");
+  c->parity ^= 1;
+  ++c->steps;
+  return LB_OK;
+}
+
 int lb_closure_fallbacks(lb_ctx *c, long long *count) {
   LB_CHECK_CTX(c);
   if (!count) return fail(c, LB_EINVAL, "null argument");

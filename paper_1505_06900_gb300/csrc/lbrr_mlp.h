@@ -179,10 +179,13 @@ cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid
 // updates the cell in place (closure_update_cell), so no prediction goes
 // through device memory. On a timeout (*status = 1) part of the cells have
 // not been updated.
+// With trace (inspection only): also trace [N][kConvTrace] per cell: the
+// FP32 activations of layers 1 and 2 and the 17 standardised predictions.
+constexpr int kConvTrace = 2 * kMlpHidden + kMlpOutUsed;  // 145
 cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
                                  float *f, float om1, int parity, unsigned long long *fallbacks,
                                  float bound, float dead_zone, int *status, int nblocks,
-                                 cudaStream_t st);
+                                 cudaStream_t st, float *trace = nullptr);
 // One update of an FP32 D3Q27 store with the learned correction: ystd [17][N]
 // holds the network's standardised predictions for the current populations.
 cudaError_t launch_step_delta(const MlpDevice &p, float *f, const Grid &g, float om1, int parity,

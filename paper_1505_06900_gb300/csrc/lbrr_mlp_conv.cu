@@ -122,20 +122,25 @@ __device__ __forceinline__ bool group_any(int g, bool pred) {
 }
 
 // tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v) into row r
-// of a K = 64 operand (canonical layout), BF16
+// of a K = 64 operand (canonical layout), BF16; with TRACE also the FP32
+// values into trace_row[c0 ..].
+template <bool TRACE = false>
 __device__ __forceinline__ void hidden_half(const uint32_t (&v)[32], const float *bias, int c0,
-                                            unsigned char *dst, int r) {
+                                            unsigned char *dst, int r,
+                                            float *trace_row = nullptr) {
 #pragma unroll
   for (int k = 0; k < 32; k += 8) {
+    float h[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) h[e] = tanh_approx(__uint_as_float(v[k + e]) + bias[c0 + k + e]);
+    if (TRACE)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) trace_row[c0 + k + e] = h[e];
     uint4 q;
-    q.x = pack_bf16(tanh_approx(__uint_as_float(v[k]) + bias[c0 + k]),
-                    tanh_approx(__uint_as_float(v[k + 1]) + bias[c0 + k + 1]));
-    q.y = pack_bf16(tanh_approx(__uint_as_float(v[k + 2]) + bias[c0 + k + 2]),
-                    tanh_approx(__uint_as_float(v[k + 3]) + bias[c0 + k + 3]));
-    q.z = pack_bf16(tanh_approx(__uint_as_float(v[k + 4]) + bias[c0 + k + 4]),
-                    tanh_approx(__uint_as_float(v[k + 5]) + bias[c0 + k + 5]));
-    q.w = pack_bf16(tanh_approx(__uint_as_float(v[k + 6]) + bias[c0 + k + 6]),
-                    tanh_approx(__uint_as_float(v[k + 7]) + bias[c0 + k + 7]));
+    q.x = pack_bf16(h[0], h[1]);
+    q.y = pack_bf16(h[2], h[3]);
+    q.z = pack_bf16(h[4], h[5]);
+    q.w = pack_bf16(h[6], h[7]);
     *reinterpret_cast<uint4 *>(dst + cm_offset(r, c0 + k, kMlpHidden)) = q;
   }
 }
@@ -148,11 +153,15 @@ __device__ __forceinline__ void load_acc32(uint32_t taddr, uint32_t (&v)[32]) {
   tmem_wait_ld();
 }
 
-template <int PARITY, typename IDX>
+// TRACE: also trace[cell][0..63], [64..127] (the FP32 activations of layers
+// 1 and 2 before their BF16 rounding) and [128..144] (the 17 standardised
+// predictions) of every cell.
+template <int PARITY, typename IDX, bool TRACE = false>
 __global__ void __launch_bounds__(kConvThreads, 1)
     mlp_conv_kernel(MlpDevice p, const __grid_constant__ CUtensorMap xs_map, const Grid g,
                     float *__restrict__ f, const float om1, unsigned long long *fallbacks,
-                    const float bound, const float dead_zone, int *status) {
+                    const float bound, const float dead_zone, int *status,
+                    float *__restrict__ trace) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
@@ -301,14 +310,15 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       }
       fence_after();
       uint32_t v[32];
+      float *trace_row = TRACE ? trace + ((long long)tile * kCRows + r) * kConvTrace : nullptr;
       // layer 1 epilogue (hidden row 1), releasing the accumulator once read
       load_acc32(lane_addr + c1, v);
-      hidden_half(v, sb, 0, a2, r);
+      hidden_half<TRACE>(v, sb, 0, a2, r, trace_row);
       load_acc32(lane_addr + c1 + 32, v);
       fence_before();
       group_sync(eg);
       if (leader) mbar_arrive(bar(kBarAcc1E + eg));
-      hidden_half(v, sb, 32, a2, r);
+      hidden_half<TRACE>(v, sb, 32, a2, r, trace_row);
       fence_async_smem();
       group_sync(eg);
       if (leader) {
@@ -329,9 +339,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       fence_after();
       // layer 2 epilogue (hidden row 2 over row 1, which layer 2 has read)
       load_acc32(lane_addr + c2, v);
-      hidden_half(v, sb + kMlpHidden, 0, a2, r);
+      hidden_half<TRACE>(v, sb + kMlpHidden, 0, a2, r, TRACE ? trace_row + kMlpHidden : nullptr);
       load_acc32(lane_addr + c2 + 32, v);
-      hidden_half(v, sb + kMlpHidden, 32, a2, r);
+      hidden_half<TRACE>(v, sb + kMlpHidden, 32, a2, r, TRACE ? trace_row + kMlpHidden : nullptr);
       fence_async_smem();
       fence_before();
       group_sync(eg);
@@ -358,6 +368,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       float yk[kMlpOutUsed];
 #pragma unroll
       for (int k = 0; k < kMlpOutUsed; ++k) yk[k] = __uint_as_float(v[k]) + b3[k];
+      if (TRACE)
+#pragma unroll
+        for (int k = 0; k < kMlpOutUsed; ++k) trace_row[2 * kMlpHidden + k] = yk[k];
       const uint32_t t = (uint32_t)tile, tpr = (uint32_t)g.nx / kCRows;
       const uint32_t row = t / tpr;
       const int x = (int)(t - row * tpr) * kCRows + r;
@@ -459,11 +472,13 @@ cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid
 cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, const Grid &g,
                                  float *f, float om1, int parity, unsigned long long *fallbacks,
                                  float bound, float dead_zone, int *status, int nblocks,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, float *trace) {
   // 32-bit element offsets where every slot of the store is addressable so
-  auto kern = 27 * g.n < (1LL << 31) ? (parity ? mlp_conv_kernel<1, int> : mlp_conv_kernel<0, int>)
-                                     : (parity ? mlp_conv_kernel<1, long long>
-                                               : mlp_conv_kernel<0, long long>);
+  auto kern = trace ? (parity ? mlp_conv_kernel<1, long long, true>
+                              : mlp_conv_kernel<0, long long, true>)
+              : 27 * g.n < (1LL << 31) ? (parity ? mlp_conv_kernel<1, int> : mlp_conv_kernel<0, int>)
+                                       : (parity ? mlp_conv_kernel<1, long long>
+                                                 : mlp_conv_kernel<0, long long>);
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
   if (e != cudaSuccess) return e;
@@ -472,7 +487,7 @@ cudaError_t launch_mlp_conv_step(const MlpDevice &p, const CUtensorMap &map, con
   const int nb = (int)(tiles < nblocks ? tiles : nblocks);
   if (nb < 1) return cudaSuccess;
   kern<<<nb, kConvThreads, kConvSmem, st>>>(p, map, g, f, om1, fallbacks, bound, dead_zone,
-                                            status);
+                                            status, trace);
   return cudaGetLastError();
 }
 

@@ -71,14 +71,15 @@ def to_dev_bf16(X):
     return torch.from_numpy(X.astype(np.float32)).cuda().to(torch.bfloat16)
 
 
-def check_forward_chain(X, p, H1, H2, Y):
+def check_forward_chain(X, p, H1, H2, Y, k1=288):
     """Layer-by-layer check of a kernel's activations H1, H2 (FP32, before the
     BF16 rounding) and outputs Y against the FP64 reference; returns the
-    reference values and bounds the backward checks build on."""
+    reference values and bounds the backward checks build on. k1: the number
+    of layer-1 product terms the kernel accumulates (padding included)."""
     aX = np.abs(X)
     z1 = X @ p["W1"].T + p["b1"]
     t1 = np.tanh(z1)
-    b_h1 = ETANH * np.abs(t1) + acc(288) * (aX @ np.abs(p["W1"]).T + np.abs(p["b1"]))
+    b_h1 = ETANH * np.abs(t1) + acc(k1) * (aX @ np.abs(p["W1"]).T + np.abs(p["b1"]))
     assert np.all(np.abs(H1 - t1) <= b_h1), np.max(np.abs(H1 - t1) / b_h1)
     A1 = C.bf16_round(H1)  # the kernel's rounding, one of the correct ones
     z2 = A1 @ p["W2"].T + p["b2"]
@@ -449,6 +450,58 @@ def test_closure_step_with_a_dead_zone_matches_oracle(shape):
         a.step(3)
         b.step(3)
         assert np.array_equal(a.populations().cpu().numpy(), b.populations().cpu().numpy())
+    net.close()
+
+
+# (128, 3, 3): one tile per row, three rows of tiles; (256, 16, 16): 512 tiles,
+# several per block (stage and accumulator reuse, every epilogue group)
+@pytest.mark.parametrize("shape", [(128, 3, 3), (256, 16, 16)])
+def test_fused_closure_step_layer_by_layer(shape):
+    """The fused closure update, each stage against the FP64 reference with a
+    tight bound (the inspection form lb_closure_step_trace returns what the
+    kernels computed): the feature source is the BF16 rounding of the
+    standardised moments of every cell and halo position; the 27-tap
+    convolution, the hidden layer and the output layer follow the network
+    checks above from those features; the corrected update from the kernel's
+    predictions (shrunk by the dead zone) matches the reference collision and
+    streaming to FP32 precision."""
+    shape, tau, df, p, mean, inv, out_scale = _closure_case(62, 2e-5, shape)
+    theta = 0.3
+    net = B.MLP(C.pack(p))
+    net.set_scaling(mean, inv, out_scale)
+    with B.Solver(B.D3Q27, shape, tau) as s:
+        s.set_populations(torch.from_numpy(df).cuda())
+        s.set_closure(net, bound=1e6, dead_zone=theta)
+        tr, xs = s.closure_step_trace()
+        got = s.populations().cpu().numpy()
+        assert s.closure_fallbacks() == 0
+    tr = tr.cpu().numpy().astype(np.float64)
+    xs = xs.float().cpu().numpy().astype(np.float64)
+    nx, ny, nz = shape
+    f = f64_state(O.D3Q27, df)
+    m64, i64, o64 = (np.asarray(v, np.float32).astype(np.float64) for v in (mean, inv, out_scale))
+    # features: standardised moments, BF16, periodic halo, six zero channels
+    z = (C.moment_field(f) - m64[:, None, None, None]) * i64[:, None, None, None]
+    zp = np.pad(z, ((0, 0), (1, 1), (1, 1), (1, 1)), mode="wrap")
+    got_feat = np.moveaxis(xs[..., :10], -1, 0)
+    ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(zp), 1e-30))) - 7)
+    assert np.all(np.abs(got_feat - zp) <= ulp + 1e-5)
+    assert np.all(xs[..., 10:] == 0)
+    # the network rows from the kernel's features (feature 10 nb + k of a cell
+    # is moment k of neighbour nb = (dx+1) + 3 (dy+1) + 9 (dz+1))
+    X = np.zeros((nx * ny * nz, 288))
+    for nb in range(27):
+        dx, dy, dz = nb % 3 - 1, (nb // 3) % 3 - 1, nb // 9 - 1
+        blk = got_feat[:, 1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        X[:, 10 * nb:10 * nb + 10] = blk.reshape(10, -1).T
+    Y = np.zeros((X.shape[0], 32))
+    Y[:, :17] = tr[:, 128:145]
+    check_forward_chain(X, p, tr[:, :64], tr[:, 64:128], Y, k1=27 * 16)
+    # the update from the kernel's predictions
+    yd = np.sign(Y[:, :17]) * np.maximum(np.abs(Y[:, :17]) - theta, 0.0)
+    assert np.count_nonzero(yd) > 0.1 * yd.size  # the dead zone leaves a correction
+    ref = C.step_with_delta(f, tau, yd * o64)
+    assert max_rel_to_weight(O.D3Q27, got, shifted(O.D3Q27, ref)) <= 1e-6
     net.close()
 
 
