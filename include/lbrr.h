@@ -32,7 +32,10 @@
  *  - Populations exchanged with the caller are "shifted": df_i = f_i - w_i,
  *    float32, one array of Q * nx * ny * nz values.
  *  - Pointers documented as device pointers must point to memory of the
- *    context's device (cudaMalloc, torch tensors); the caller owns them.
+ *    context's device (cudaMalloc, torch tensors) or managed memory; the
+ *    caller owns them. Each call checks them (cudaPointerGetAttributes,
+ *    which allocates nothing) and answers LB_EINVAL, before any kernel runs,
+ *    for a host pointer or another device's memory.
  *  - All work is ordered on the context's stream (lb_set_stream); calls that
  *    return values to host memory synchronise that stream.
  *  - Every call returns LB_OK or an error code; on error the context's state

@@ -105,6 +105,31 @@ struct DeviceGuard {
   }
 };
 
+// Whether p is memory that device dev can use as its own: device memory of
+// dev, or managed memory (cudaPointerGetAttributes allocates nothing).
+bool usable_on(const void *p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
+}
+
+// LB_OK, or LB_EINVAL naming the argument when p is not usable on the
+// context's device; null pointers are left to the caller's own checks.
+int need_device(lb_ctx *c, const void *p, const char *what) {
+  if (!p || usable_on(p, c->device)) return LB_OK;
+  return fail(c, LB_EINVAL, "%s must be device memory of device %d (got a host pointer or "
+              "another device's memory)", what, c->device);
+}
+
+#define LB_NEED_DEVICE(c, p)                   \
+  do {                                         \
+    const int rc_ = need_device((c), (p), #p); \
+    if (rc_ != LB_OK) return rc_;              \
+  } while (0)
+
 int free_all(lb_ctx *c) {
   for (auto &ge : c->graph)
     if (ge) cudaGraphExecDestroy(ge);
@@ -290,6 +315,8 @@ int lb_init_fields(lb_ctx *c, const float *rho, const float *u, int init_mode) {
   if (!rho || !u) return fail(c, LB_EINVAL, "rho and u must be device pointers");
   if (init_mode != LB_INIT_EQ && init_mode != LB_INIT_EQ_NEQ_FD)
     return fail(c, LB_EINVAL, "unknown init mode %d", init_mode);
+  LB_NEED_DEVICE(c, rho);
+  LB_NEED_DEVICE(c, u);
   DeviceGuard dg(c->device);
   cudaError_t e = lbrr::launch_init(c->q, c->storage, c->collision, c->f, c->g, rho, u,
                                     (float)c->tau, init_mode, c->stream);
@@ -391,6 +418,9 @@ int lb_moments(lb_ctx *c, float *rho, float *u, float *pi1) {
   Range nvtx_range("lb_moments");
   LB_CHECK_CTX(c);
   if (!rho && !u && !pi1) return LB_OK;
+  LB_NEED_DEVICE(c, rho);
+  LB_NEED_DEVICE(c, u);
+  LB_NEED_DEVICE(c, pi1);
   DeviceGuard dg(c->device);
   cudaError_t e =
       lbrr::launch_moments(c->q, c->storage, c->f, c->g, c->parity, rho, u, pi1, c->stream);
@@ -429,6 +459,7 @@ int lb_enstrophy(lb_ctx *c, double *out) {
 int lb_get_populations(lb_ctx *c, float *dst) {
   LB_CHECK_CTX(c);
   if (!dst) return fail(c, LB_EINVAL, "null destination");
+  LB_NEED_DEVICE(c, dst);
   DeviceGuard dg(c->device);
   cudaError_t e =
       lbrr::launch_get_populations(c->q, c->storage, c->f, c->g, c->parity, dst, c->stream);
@@ -439,6 +470,7 @@ int lb_get_populations(lb_ctx *c, float *dst) {
 int lb_set_populations(lb_ctx *c, const float *src) {
   LB_CHECK_CTX(c);
   if (!src) return fail(c, LB_EINVAL, "null source");
+  LB_NEED_DEVICE(c, src);
   DeviceGuard dg(c->device);
   cudaError_t e = lbrr::launch_set_populations(c->q, c->storage, c->f, c->g, src, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_populations launch");
@@ -544,6 +576,20 @@ static int mlp_fail(lb_mlp *m, int code, const char *fmt, ...) {
   va_end(ap);
   return code;
 }
+
+// LB_OK, or LB_EINVAL naming the argument when p is not usable on the
+// network's device; null pointers are left to the caller's own checks.
+static int mlp_need_device(lb_mlp *m, const void *p, const char *what) {
+  if (!p || usable_on(p, m->device)) return LB_OK;
+  return mlp_fail(m, LB_EINVAL, "%s must be device memory of device %d (got a host pointer or "
+                  "another device's memory)", what, m->device);
+}
+
+#define LB_MLP_NEED_DEVICE(m, p)                   \
+  do {                                             \
+    const int rc_ = mlp_need_device((m), (p), #p); \
+    if (rc_ != LB_OK) return rc_;                  \
+  } while (0)
 
 void lb_mlp_destroy(lb_mlp *m) {
   if (!m) return;
@@ -676,6 +722,9 @@ int lb_mlp_set_scaling(lb_mlp *m, const float *in_mean, const float *in_inv_std,
 
 static int mlp_forward(lb_mlp *m, const void *X, long long M, float *Y, float *H) {
   if (!m || !X || !Y || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
+  LB_MLP_NEED_DEVICE(m, X);
+  LB_MLP_NEED_DEVICE(m, Y);
+  LB_MLP_NEED_DEVICE(m, H);
   DeviceGuard dg(m->device);
   cudaError_t e =
       lbrr::launch_mlp_tc(m->d, X, nullptr, nullptr, M, Y, m->status, m->nblocks, m->stream, H);
@@ -695,6 +744,10 @@ int lb_mlp_forward_trace(lb_mlp *m, const void *X, long long M, float *Y, float 
 static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, float *grad,
                         int adam, float lr, double *loss, float *trace = nullptr) {
   if (!m || !X || !T || M < 1) return mlp_fail(m, LB_EINVAL, "bad argument");
+  LB_MLP_NEED_DEVICE(m, X);
+  LB_MLP_NEED_DEVICE(m, T);
+  LB_MLP_NEED_DEVICE(m, grad);
+  LB_MLP_NEED_DEVICE(m, trace);
   if (adam && !(lr > 0.f && std::isfinite(lr)))
     return mlp_fail(m, LB_EINVAL, "learning rate must be positive");
   DeviceGuard dg(m->device);
@@ -777,6 +830,7 @@ static int closure_capable(lb_ctx *c) {
 int lb_closure_features(lb_ctx *c, const lb_mlp *m, void *X) {
   LB_CHECK_CTX(c);
   if (!m || !X) return fail(c, LB_EINVAL, "null argument");
+  LB_NEED_DEVICE(c, X);
   int rc = closure_capable(c);
   if (rc == LB_OK) rc = ensure_mom(c, false);
   if (rc != LB_OK) return rc;
@@ -790,6 +844,7 @@ int lb_closure_features(lb_ctx *c, const lb_mlp *m, void *X) {
 int lb_closure_targets(lb_ctx *c, const lb_mlp *m, float *T) {
   LB_CHECK_CTX(c);
   if (!m || !T) return fail(c, LB_EINVAL, "null argument");
+  LB_NEED_DEVICE(c, T);
   int rc = closure_capable(c);
   if (rc != LB_OK) return rc;
   DeviceGuard dg(c->device);
@@ -835,6 +890,7 @@ int lb_closure_step_targets(lb_ctx *pre, lb_ctx *post, const lb_mlp *m, float *T
   LB_CHECK_CTX(pre);
   LB_CHECK_CTX(post);
   if (!m || !T) return fail(pre, LB_EINVAL, "null argument");
+  LB_NEED_DEVICE(pre, T);
   int rc = closure_capable(pre);
   if (rc == LB_OK) rc = closure_capable(post);
   if (rc != LB_OK) return rc;
@@ -886,6 +942,8 @@ int lb_set_closure(lb_ctx *c, const lb_mlp *m, float bound) {
 int lb_closure_step_trace(lb_ctx *c, float *trace, void *xs_out) {
   LB_CHECK_CTX(c);
   if (!trace || !xs_out) return fail(c, LB_EINVAL, "null trace or feature-source buffer");
+  LB_NEED_DEVICE(c, trace);
+  LB_NEED_DEVICE(c, xs_out);
   if (!c->closure || !c->xs)
     return fail(c, LB_EINVAL,
                 "needs a learned closure on a grid of whole 128-cell row tiles (lb_set_closure)");
