@@ -58,3 +58,32 @@ def test_host_pointers_are_rejected_and_the_context_survives():
     Y = net.forward(X)  # the network still runs
     assert torch.isfinite(Y).all()
     net.close()
+
+
+def test_closure_entry_points_validate_their_arguments():
+    """Invalid closure arguments are refused with LB_EINVAL and a message:
+    a non-finite off-equilibrium scale, states on different grids, a negative
+    or non-finite dead zone, and the inspection step on a context without a
+    fused closure."""
+    lib = B.load()
+    net = B.MLP()
+    with B.Solver(B.D3Q27, (8, 6, 4), 0.7) as fine, B.Solver(B.D3Q27, (4, 3, 2), 0.6) as coarse, \
+            B.Solver(B.D3Q27, (4, 3, 4), 0.6) as other:
+        assert lib.lb_coarsen_neq(fine.handle, coarse.handle, float("nan")) == B.LB_EINVAL
+        assert "neq_scale" in lib.lb_last_error(coarse.handle).decode()
+        T = torch.empty((coarse.n, 32), device="cuda")
+        assert lib.lb_closure_step_targets(coarse.handle, other.handle, net.handle,
+                                           B._ptr(T)) == B.LB_EINVAL
+        assert "grid" in lib.lb_last_error(coarse.handle).decode()
+        for dz in (-0.1, float("inf")):
+            assert lib.lb_set_closure_ex(coarse.handle, net.handle, 8.0, dz) == B.LB_EINVAL
+            assert "dead_zone" in lib.lb_last_error(coarse.handle).decode()
+    tr = torch.empty((80 * 3 * 4, 145), device="cuda")
+    xs = torch.empty((6 * 5 * 82 * 16,), dtype=torch.bfloat16, device="cuda")
+    with B.Solver(B.D3Q27, (80, 3, 4), 0.7) as s:
+        # no closure set, then a closure on rows that are not whole 128-cell tiles
+        assert lib.lb_closure_step_trace(s.handle, B._ptr(tr), B._ptr(xs)) == B.LB_EINVAL
+        s.set_closure(net)
+        assert lib.lb_closure_step_trace(s.handle, B._ptr(tr), B._ptr(xs)) == B.LB_EINVAL
+        assert "128-cell" in lib.lb_last_error(s.handle).decode()
+    net.close()
