@@ -205,7 +205,8 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    n_sample = 32
+    # the same sample grid as the GPU arm's cpu_baseline (a 1/64 sample of 512^3)
+    n_sample = args.cpu_sample
     res = oracle_sample(args.steps, args.warmup, n_sample)
     line = {
         "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
