@@ -805,11 +805,15 @@ static int ensure_mom(lb_ctx *c, bool for_step) {
   if (e == cudaSuccess && conv && !c->xs) {
     e = cudaMalloc(&c->xs, lbrr::feature_source_bytes(c->g));
     if (e == cudaSuccess) {
-      e = lbrr::make_feature_map(c->xs, c->g, &c->xs_map);
-      if (e != cudaSuccess) {
+      // the row padding beyond the halo is copied by the last tile of a row
+      // but read by no MMA: zero it once
+      cudaError_t ez = cudaMemset(c->xs, 0, lbrr::feature_source_bytes(c->g));
+      if (ez == cudaSuccess) ez = lbrr::make_feature_map(c->xs, c->g, &c->xs_map);
+      if (ez != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(c->xs);
         c->xs = nullptr;
-        return fail(c, LB_ECUDA, "cannot encode the feature-source tensor map");
+        return fail(c, LB_ECUDA, "cannot prepare the feature source or its tensor map");
       }
     }
   }
@@ -957,8 +961,7 @@ int lb_closure_step_trace(lb_ctx *c, float *trace, void *xs_out) {
                                    c->closure_dead_zone, c->closure->status,
                                    c->closure->nblocks, c->stream, trace);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(xs_out, c->xs, lbrr::feature_source_bytes(c->g), cudaMemcpyDeviceToDevice,
-                        c->stream);
+    e = lbrr::launch_export_features(c->xs, c->g, xs_out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "closure step trace");
   c->parity ^= 1;
   ++c->steps;

@@ -54,36 +54,35 @@ __host__ __device__ constexpr int hi_pow(int k, int axis) {
   return axis == 0 ? code[k] % 3 : (axis == 1 ? (code[k] / 3) % 3 : code[k] / 9);
 }
 
-// The closure update of cell (x, y, z) of an FP32 D3Q27 AA store (parity as
-// in lbrr_step.cu): the RR coefficients plus (1 - 1/tau) times the network's
-// correction, y'[k] out_scale[k] added to coefficient k of orders 3..6, with
-// y' = sign(y) max(|y| - dead_zone, 0) the standardised prediction y = ystd[k]
-// shrunk by the dead zone; plain RR for the cell (counted in *fallbacks) when a
-// standardised prediction exceeds the bound (or is not a number) or a
-// corrected population is not positive. Each cell reads exactly the locations it writes. IDX is
-// the type of the element offsets: int needs 27 N < 2^31 (fewer registers).
+// Element offset of the location from which the update of cell (x, y, z) of
+// an FP32 D3Q27 AA store (parity as in lbrr_step.cu) reads population i; the
+// update writes population i to the location it_writes(i) below, and the two
+// sets are the same 27 locations. IDX is the type of the element offsets:
+// int needs 27 N < 2^31 (fewer registers).
 template <int PARITY, typename IDX = long long>
-__device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *__restrict__ f,
-                                                    const Grid &g, const float om1, int x, int y,
-                                                    int z, const float (&ystd)[kMlpOutUsed],
-                                                    unsigned long long *fallbacks,
-                                                    const float bound, const float dead_zone) {
+__device__ __forceinline__ IDX closure_read_offset(const Grid &g, int x, int y, int z, int i) {
   const IDX n = (IDX)g.n;
-  const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
-  const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
-  const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
-  auto cell_at = [&](int b, int c, int a) -> IDX {
-    return ((IDX)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
-  };
-  const IDX cell = cell_at(1, 1, 1);
-  float df[27];
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    if (PARITY == 0)
-      df[i] = f[i * n + cell];
-    else
-      df[i] = f[(26 - i) * n + cell_at(1 - vel(i, 1), 1 - vel(i, 2), 1 - vel(i, 0))];
-  }
+  if (PARITY == 0) return (IDX)i * n + ((IDX)z * g.ny + y) * g.nx + x;
+  const int xa = wrap_add(x, -vel(i, 0), g.nx), ya = wrap_add(y, -vel(i, 1), g.ny),
+            za = wrap_add(z, -vel(i, 2), g.nz);
+  return (IDX)(26 - i) * n + ((IDX)za * g.ny + ya) * g.nx + xa;
+}
+
+// The closure update of cell (x, y, z) of an FP32 D3Q27 AA store from its 27
+// logical populations df (read at closure_read_offset): the RR coefficients
+// plus (1 - 1/tau) times the network's correction, y'[k] out_scale[k] added
+// to coefficient k of orders 3..6, with y' = sign(y) max(|y| - dead_zone, 0)
+// the standardised prediction y = ystd[k] shrunk by the dead zone; plain RR
+// for the cell (counted in *fallbacks) when a standardised prediction exceeds
+// the bound (or is not a number) or a corrected population is not positive.
+// Each cell writes exactly the locations it reads.
+template <int PARITY, typename IDX = long long>
+__device__ __forceinline__ void closure_update_cell_df(const MlpDevice &p, float *__restrict__ f,
+                                                       const Grid &g, const float om1, int x,
+                                                       int y, int z, const float (&df)[27],
+                                                       const float (&ystd)[kMlpOutUsed],
+                                                       unsigned long long *fallbacks,
+                                                       const float bound, const float dead_zone) {
   const Macro m = Lattice<27>::moments(df);
   bool use = true;
   float cc[3][3][3];
@@ -106,6 +105,14 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
     synth_tensor_d3q27<false>(cc, out);
     if (fallbacks) atomicAdd(fallbacks, 1ull);
   }
+  const IDX n = (IDX)g.n;
+  const int xs3[3] = {wrap_add(x, -1, g.nx), x, wrap_add(x, 1, g.nx)};
+  const int ys3[3] = {wrap_add(y, -1, g.ny), y, wrap_add(y, 1, g.ny)};
+  const int zs3[3] = {wrap_add(z, -1, g.nz), z, wrap_add(z, 1, g.nz)};
+  auto cell_at = [&](int b, int c, int a) -> IDX {
+    return ((IDX)zs3[c] * g.ny + ys3[b]) * g.nx + xs3[a];
+  };
+  const IDX cell = cell_at(1, 1, 1);
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     if (PARITY == 0)
@@ -113,6 +120,20 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
     else
       f[i * n + cell_at(1 + vel(i, 1), 1 + vel(i, 2), 1 + vel(i, 0))] = out[i];
   }
+}
+
+// The same, reading the populations itself.
+template <int PARITY, typename IDX = long long>
+__device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *__restrict__ f,
+                                                    const Grid &g, const float om1, int x, int y,
+                                                    int z, const float (&ystd)[kMlpOutUsed],
+                                                    unsigned long long *fallbacks,
+                                                    const float bound, const float dead_zone) {
+  float df[27];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) df[i] = f[closure_read_offset<PARITY, IDX>(g, x, y, z, i)];
+  closure_update_cell_df<PARITY, IDX>(p, f, g, om1, x, y, z, df, ystd, fallbacks, bound,
+                                      dead_zone);
 }
 
 size_t mlp_train_smem();
@@ -167,13 +188,16 @@ cudaError_t launch_mlp_tc(const MlpDevice &p, const void *X, const float *mom, c
                           float *H = nullptr);
 // The TMA-fed, pipelined forward pass (lbrr_mlp_conv.cu) for grids whose
 // rows are whole 128-cell tiles: the feature source xs (standardised moments,
-// BF16, 16 channels, one-cell periodic halo: feature_source_bytes(g) bytes),
-// its tensor map, and the network on it.
+// BF16, one-cell periodic halo, in the two 8-channel halves that kernel
+// reads: feature_source_bytes(g) bytes), its tensor map, and the network on
+// it. launch_export_features writes the feature source channels-last,
+// [(nx + 2)(ny + 2)(nz + 2)][16] BF16 (channels 10..15 zero).
 bool mlp_conv_supported(const Grid &g);
 size_t feature_source_bytes(const Grid &g);
 cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map);
 cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid &g, int parity,
                                   void *xs, cudaStream_t st);
+cudaError_t launch_export_features(const void *xs, const Grid &g, void *out, cudaStream_t st);
 // The network fused with the closure update: the thread that owns a
 // tile row takes its cell's 17 predictions from the layer-3 accumulator and
 // updates the cell in place (closure_update_cell), so no prediction goes

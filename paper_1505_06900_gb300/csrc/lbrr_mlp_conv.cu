@@ -4,32 +4,45 @@
 //
 // Layer 1 of the network is a 3x3x3 convolution of the standardised moment
 // field: its 270 inputs for a cell are the 10 moments of the 27 cells around
-// it. A feature-source tensor holds those moments once per cell, standardised
-// and rounded to BF16, channels-last with 16 channels (10 used) and a one-cell
-// periodic halo: xs[z + 1][y + 1][x + 1][16]. For a tile of 128 cells
-// x0 .. x0 + 127 of row (y, z) the kernel copies, per neighbour row
-// (y + dy, z + dz), the 130 positions x0 - 1 .. x0 + 128 with two TMA tile
-// loads (channels 0-7 and 8-15), which lands them as [130 rows][16 bytes]:
-// the canonical K-major layout without swizzle (8-row groups 128 bytes
-// apart, the two channel halves one row block apart). The 27 MMAs of layer
-// 1 (M 128, N 64, K 16, one per neighbour (dx, dy, dz)) read that block
-// starting dx + 1 rows in; the weight operand of each neighbour is W1's 10
-// columns of that neighbour, zero-padded to 16.
+// it. A feature-source tensor holds those moments once per position of the
+// grid with a one-cell periodic halo (X = x + 1, Y = y + 1, Z = z + 1), BF16,
+// split in two halves of 8 channels, each half laid out [Z][Y][X][8] with
+// rows padded to nx + 8 positions:
+//   half 0: moments 0..7 (rho - 1, ux, uy, uz, Pi xx, xy, xz, yy) at X;
+//   half 1: moments 8, 9 (Pi yz, zz) at X - 1, X and X + 1, then two zeros.
+// For a tile of 128 cells x0 .. x0 + 127 of row (y, z) the producer copies,
+// per half, the 3 x 3 neighbour rows Y = y .. y + 2, Z = z .. z + 2 over the
+// positions X = x0 .. x0 + 135 in one TMA tile load whose rows are 128-byte
+// chunks of 8 positions. In shared memory each neighbour row is then
+// [136 positions][16 bytes]: the canonical K-major layout without swizzle
+// (8-row groups 128 bytes apart) with position X = x0 + r at row r, so that
+// a cell's neighbour at dx is row m + dx + 1 of its tile row m. Layer 1 is
+// 18 MMAs (M 128, N 64, K 16, K = 288 in all), two per neighbour row, each
+// reading two 8-channel K blocks through the leading byte offset of its
+// descriptor: (half 0 at dx = -1, half 0 at dx = 0), 16 bytes apart, and
+// (half 0 at dx = +1, half 1 at dx = 0), the latter holding moments 8 and 9
+// of all three dx. The weight operand of each MMA is W1's 16 matching
+// columns.
 //
 // One persistent block per SM, eighteen warps:
-//   warp 0      TMA producer: 18 tile loads per tile into one of 2 stages
+//   warp 0      TMA producer: 2 tile loads per tile into one of 2 stages
 //   warp 1      layer-1 MMA issuer (and TMEM owner)
 //   warps 2-17  four epilogue groups of four warps taking every fourth tile;
-//               each reads its layer-1 accumulator (thread = TMEM lane = tile
-//               row), applies bias and tanh, writes the BF16 hidden row,
-//               issues layers 2 and 3 itself and, with the 17 standardised
-//               outputs of its row, performs the closure update of that
-//               row's cell in the population store (closure_update_cell):
-//               the step of the learned closure is fused into the network.
+//               thread = TMEM lane = tile row. When a group starts a tile,
+//               each thread sends the 27 populations its cell's update reads
+//               to shared memory (cp.async). The group then reads its layer-1
+//               accumulator, applies bias and tanh and stores the BF16
+//               hidden row back into tensor memory, where layer 2 takes it
+//               as its A operand (issued by the group); the same for layer
+//               2 and layer 3. With the 17 standardised outputs of its row
+//               and the staged populations each thread performs the closure
+//               update of its cell in the population store
+//               (closure_update_cell_df): the step of the learned closure is
+//               fused into the network.
 // Group g owns TMEM columns 128 g .. 128 g + 127: the first 64 take its
-// layer-1 accumulator (released as soon as the group has read it, so the
-// next tile's layer 1 can start), the other 64 its layer 2 and then layer 3.
-// Every barrier is waited on by one role in the order of its phases.
+// layer-1 accumulator and then the hidden rows h1 and h2 (32 columns), and
+// go back to the layer-1 MMAs once layer 3 has read h2; the other 64 take
+// its layer 2 and then layer 3.
 // Stages, accumulators and epilogue groups are handed over with mbarriers;
 // every wait is bounded (status[1] can shorten the main-loop limit to test
 // the timeout path). On a timeout the block raises a shared abort flag,
@@ -52,27 +65,33 @@ namespace {
 using namespace tc;
 
 constexpr int kCRows = 128;                         // cells per tile
-constexpr int kCSpan = kCRows + 2;                  // staged positions x0 - 1 .. x0 + 128
-constexpr uint32_t kHalfBytes = kCSpan * 16;        // one channel half of a neighbour row
-constexpr uint32_t kHalfPitch = 2176;               // the same, 128-byte aligned
-constexpr uint32_t kStageBytes = 18 * kHalfPitch;   // 9 neighbour rows x 2 halves
-constexpr uint32_t kTxBytes = 18 * kHalfBytes;      // bytes a stage receives
+constexpr int kChunk = 8;                           // positions per 128-byte TMA row
+constexpr int kRowPos = 136;                        // staged positions x0 - 1 .. x0 + 134
+constexpr int kPadPos = 8;                          // padded row: nx + 8 positions
+constexpr uint32_t kRowBytes = kRowPos * 16;        // one neighbour row of one half
+constexpr uint32_t kHalfBytes = 9 * kRowBytes;      // the 9 neighbour rows of one half
+constexpr uint32_t kStageBytes = 2 * kHalfBytes;
+constexpr uint32_t kTxBytes = kStageBytes;          // bytes a stage receives
 constexpr int kStages = 2;
-constexpr int kTaps = 27;
-constexpr uint32_t kTapBytes = 2 * kMlpHidden * 16;  // W1 block of one neighbour
-constexpr uint32_t kA2Bytes = kCRows * kMlpHidden * 2;
+constexpr int kMmas1 = 18;                          // layer-1 MMAs, K = 16 each
+constexpr uint32_t kW1Bytes = 2 * kMlpHidden * 16;  // W1 block of one layer-1 MMA
+static_assert(kRowPos % kChunk == 0 && kRowPos >= kCRows + 2, "staged row covers the taps");
+static_assert(kPadPos % kChunk == 0 && kPadPos >= kRowPos - kCRows, "last box inside the row");
+constexpr uint32_t kPopBytes = 27 * kCRows * 4;    // populations of one tile, [27][128]
 constexpr int kGroups = 4;                          // epilogue groups
-constexpr int kConvThreads = 32 * (2 + 4 * kGroups);
+constexpr int kIssuers = 1;                         // layer-1 MMA warps
+constexpr int kEpiWarp0 = 1 + kIssuers;             // first warp of the epilogue groups
+constexpr int kConvThreads = 32 * (kEpiWarp0 + 4 * kGroups);
 constexpr uint32_t kTmemCols = 512;
 
 constexpr uint32_t kOffW1 = 0;
-constexpr uint32_t kOffW2 = kOffW1 + kTaps * kTapBytes;
+constexpr uint32_t kOffW2 = kOffW1 + kMmas1 * kW1Bytes;
 constexpr uint32_t kOffW3 = kOffW2 + kMlpHidden * kMlpHidden * 2;
 constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
-constexpr uint32_t kOffA2 = kOffA1 + kStages * kStageBytes;
-constexpr uint32_t kOffMisc = kOffA2 + kGroups * kA2Bytes;
+constexpr uint32_t kOffPop = kOffA1 + kStages * kStageBytes;
+constexpr uint32_t kOffMisc = kOffPop + kGroups * kPopBytes;
 constexpr uint32_t kConvSmem = kOffMisc + 1024;
-static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfPitch % 128 == 0,
+static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfBytes % 128 == 0,
               "TMA destinations are 128-byte aligned");
 static_assert(kConvSmem <= 232448, "fits the shared memory of one block");
 
@@ -84,10 +103,11 @@ enum : int {
   kBarAcc1E = kBarAcc1F + kGroups,    // [groups] layer-1 accumulator read by its group
   kBarL2 = kBarAcc1E + kGroups,       // [groups] layer 2 done
   kBarL3 = kBarL2 + kGroups,          // [groups] layer 3 done
-  kBarDrain = kBarL3 + kGroups,       // [1 + groups] drain of each MMA issuer after an abort
-  kNumBars = kBarDrain + 1 + kGroups
+  kBarDrain = kBarL3 + kGroups,       // [issuers + groups] drain of each MMA issuer after an abort
+  kNumBars = kBarDrain + kIssuers + kGroups
 };
-static_assert(kNumBars * 8 + 16 <= 256, "barriers, TMEM slot and counters before the biases");
+static_assert(kNumBars * 8 + 8 + 4 * (1 + kIssuers) <= 256,
+              "barriers, TMEM slot, abort flag and counters before the biases");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
@@ -96,13 +116,14 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
                : "memory");
 }
-// 4-D tiled TMA load (coordinates innermost first), completing on mbar
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, int c3, uint32_t mbar) {
+// 5-D tiled TMA load (coordinates innermost first), completing on mbar
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, int c3, int c4, uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(mbar)
       : "memory");
 }
 // barrier of one epilogue group (4 warps, named barrier 1 + g)
@@ -121,28 +142,31 @@ __device__ __forceinline__ bool group_any(int g, bool pred) {
   return r != 0;
 }
 
-// tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v) into row r
-// of a K = 64 operand (canonical layout), BF16; with TRACE also the FP32
-// values into trace_row[c0 ..].
+// tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v), rounded
+// to BF16 and packed two to a column into the 16 TMEM columns at taddr of
+// this thread's lane (the row of the next layer's A operand); with TRACE also
+// the FP32 values into trace_row[c0 ..].
 template <bool TRACE = false>
-__device__ __forceinline__ void hidden_half(const uint32_t (&v)[32], const float *bias, int c0,
-                                            unsigned char *dst, int r,
-                                            float *trace_row = nullptr) {
+__device__ __forceinline__ void hidden_tmem(const uint32_t (&v)[32], const float *bias, int c0,
+                                            uint32_t taddr, float *trace_row = nullptr) {
+  uint32_t q[16];
 #pragma unroll
-  for (int k = 0; k < 32; k += 8) {
-    float h[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) h[e] = tanh_approx(__uint_as_float(v[k + e]) + bias[c0 + k + e]);
-    if (TRACE)
-#pragma unroll
-      for (int e = 0; e < 8; ++e) trace_row[c0 + k + e] = h[e];
-    uint4 q;
-    q.x = pack_bf16(h[0], h[1]);
-    q.y = pack_bf16(h[2], h[3]);
-    q.z = pack_bf16(h[4], h[5]);
-    q.w = pack_bf16(h[6], h[7]);
-    *reinterpret_cast<uint4 *>(dst + cm_offset(r, c0 + k, kMlpHidden)) = q;
+  for (int k = 0; k < 32; k += 4) {
+    const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + k);
+    const float h0 = tanh_approx(__uint_as_float(v[k]) + b.x);
+    const float h1 = tanh_approx(__uint_as_float(v[k + 1]) + b.y);
+    const float h2 = tanh_approx(__uint_as_float(v[k + 2]) + b.z);
+    const float h3 = tanh_approx(__uint_as_float(v[k + 3]) + b.w);
+    if (TRACE) {
+      trace_row[c0 + k] = h0;
+      trace_row[c0 + k + 1] = h1;
+      trace_row[c0 + k + 2] = h2;
+      trace_row[c0 + k + 3] = h3;
+    }
+    q[k / 2] = pack_bf16(h0, h1);
+    q[k / 2 + 1] = pack_bf16(h2, h3);
   }
+  tmem_st16(taddr, q);
 }
 
 __device__ __forceinline__ void load_acc32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -167,25 +191,34 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc + kNumBars * 8);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  int *counts = reinterpret_cast<int *>(tmem_slot + 2);  // loads issued, stages landed
+  int *counts = reinterpret_cast<int *>(tmem_slot + 2);  // loads issued, landed per issuer
   float *sb = reinterpret_cast<float *>(smem + kOffMisc + 256);  // b1, b2, b3
   auto bar = [&](int k) -> uint32_t { return smem_u32(bars + k); };
 
   // ---- weights (canonical layouts) and biases
-  for (int q = tid; q < kTaps * 2 * kMlpHidden; q += kConvThreads) {
-    const int tap = q / (2 * kMlpHidden), rem = q - tap * 2 * kMlpHidden;
+  // layer-1 MMA q = 2 r9 + kind of neighbour row r9 = (dy + 1) + 3 (dz + 1),
+  // K block h: feature 10 nb + ch of neighbour nb = (dx + 1) + 3 r9, as the
+  // A operand's blocks hold them (see above)
+  for (int q = tid; q < kMmas1 * 2 * kMlpHidden; q += kConvThreads) {
+    const int mq = q / (2 * kMlpHidden), rem = q - mq * 2 * kMlpHidden;
     const int h = rem / kMlpHidden, n = rem - h * kMlpHidden;
-    uint32_t w[4];
+    const int r9 = mq >> 1, kind = mq & 1;
+    uint16_t w[8];
 #pragma unroll
-    for (int c = 0; c < 8; c += 2) {
-      const int k0 = 8 * h + c;
-      const __nv_bfloat16 *src = p.w1 + n * kMlpIn + kMlpMoments * tap + k0;
-      const uint16_t lo = k0 < kMlpMoments ? __bfloat16_as_ushort(src[0]) : 0;
-      const uint16_t hi = k0 + 1 < kMlpMoments ? __bfloat16_as_ushort(src[1]) : 0;
-      w[c / 2] = (uint32_t)lo | ((uint32_t)hi << 16);
+    for (int k = 0; k < 8; ++k) {
+      int nb, ch;
+      if (kind == 0 || h == 0) {  // moments 0..7 of dx = -1 / 0 (kind 0), dx = +1 (kind 1)
+        nb = (kind == 0 ? h : 2) + 3 * r9;
+        ch = k;
+      } else {  // moments 8, 9 of dx = -1, 0, +1, then zeros
+        nb = k < 6 ? (k >> 1) + 3 * r9 : -1;
+        ch = 8 + (k & 1);
+      }
+      w[k] = nb >= 0 ? __bfloat16_as_ushort(p.w1[n * kMlpIn + kMlpMoments * nb + ch]) : 0;
     }
-    *reinterpret_cast<uint4 *>(smem + kOffW1 + tap * kTapBytes + h * 1024 + n * 16) =
-        make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4 *>(smem + kOffW1 + mq * kW1Bytes + h * 1024 + n * 16) =
+        make_uint4(w[0] | ((uint32_t)w[1] << 16), w[2] | ((uint32_t)w[3] << 16),
+                   w[4] | ((uint32_t)w[5] << 16), w[6] | ((uint32_t)w[7] << 16));
   }
   for (int c = tid; c < kMlpHidden * (kMlpHidden / 8); c += kConvThreads) {
     const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
@@ -205,7 +238,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(k)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     *abort_flag = 0;
-    counts[0] = counts[1] = 0;
+    for (int k = 0; k <= kIssuers; ++k) counts[k] = 0;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
@@ -244,25 +277,25 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         const uint32_t row = t / tpr;
         const int x0 = (int)(t - row * tpr) * kCRows;
         const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-#pragma unroll 1
-        for (int r9 = 0; r9 < 9; ++r9) {
-          const int dy = r9 % 3 - 1, dz = r9 / 3 - 1;
+        // padded rows Y = y .. y + 2, Z = z .. z + 2, chunks from X = x0
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
-            tma_load_4d(sa1 + s * kStageBytes + (2 * r9 + h) * kHalfPitch, &xs_map, 8 * h, x0,
-                        y + dy + 1, z + dz + 1, bar(kBarFull + s));
-        }
+        for (int h = 0; h < 2; ++h)
+          tma_load_5d(sa1 + s * kStageBytes + h * kHalfBytes, &xs_map, 0, x0 / kChunk, y, z, h,
+                      bar(kBarFull + s));
         ++issued;
       }
       counts[0] = issued;
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------- layer-1 MMA issuer
+  } else if (warp <= kIssuers) {
+    // ------------------------------------------------ layer-1 MMA issuers:
+    // warp 1 + i takes the tiles j = i mod kIssuers (stage j mod kStages)
     if (lane == 0) {
+      const int iw = warp - 1;
       int landed = 0;
-      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      for (long long tile = blockIdx.x + (long long)iw * gridDim.x; tile < ntiles;
+           tile += (long long)kIssuers * gridDim.x) {
         if (*abort_flag) break;
-        const int j = landed, s = j % kStages, gs = j % kGroups;
+        const int j = iw + kIssuers * landed, s = j % kStages, gs = j % kGroups;
         if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1, lim)) {
           *abort_flag = 1;
           break;
@@ -273,36 +306,54 @@ __global__ void __launch_bounds__(kConvThreads, 1)
           break;
         }
         fence_after();
-        // descriptors of tap 0; a tap adds its byte offset / 16 to the start
-        // address field (no carry: shared addresses stay below 256 KB)
-        const uint64_t a0 = sdesc(sa1 + s * kStageBytes, kHalfPitch, 128);
+        // descriptors of neighbour row 0; a row adds its byte offset / 16 to
+        // the start address field (no carry: shared addresses stay below
+        // 256 KB). aP: rows m, m + 1 of half 0 (dx = -1, 0); aQ: row m + 2 of
+        // half 0 (dx = +1) and row m + 1 of half 1 (moments 8, 9 of all dx).
+        const uint32_t st = sa1 + s * kStageBytes;
+        const uint64_t aP = sdesc(st, 16, 128);
+        const uint64_t aQ = sdesc(st + 32, kHalfBytes - 16, 128);
         const uint64_t b0 = sdesc(sw1, 1024, 128);
         const uint32_t d = tmem + 128 * gs;
 #pragma unroll
-        for (int tap = 0; tap < kTaps; ++tap) {
-          const uint32_t aoff = 2 * (tap / 3) * kHalfPitch + (tap % 3) * 16;
-          umma(d, a0 + (aoff >> 4), b0 + ((tap * kTapBytes) >> 4),
-               idesc_bf16(kCRows, kMlpHidden), tap > 0);
+        for (int r9 = 0; r9 < 9; ++r9) {
+          const uint32_t ro = (r9 * kRowBytes) >> 4;
+          umma(d, aP + ro, b0 + ((2 * r9 * kW1Bytes) >> 4), idesc_bf16(kCRows, kMlpHidden),
+               r9 > 0);
+          umma(d, aQ + ro, b0 + (((2 * r9 + 1) * kW1Bytes) >> 4),
+               idesc_bf16(kCRows, kMlpHidden), 1);
         }
         umma_commit(bar(kBarEmpty + s));
         umma_commit(bar(kBarAcc1F + gs));
       }
-      counts[1] = landed;
+      counts[1 + iw] = landed;
     }
-  } else {
+  } else if (warp >= kEpiWarp0) {
     // --------------------------------------------------- epilogue groups
-    const int eg = (warp - 2) >> 2;             // group 0 .. kGroups - 1
+    const int eg = (warp - kEpiWarp0) >> 2;     // group 0 .. kGroups - 1
     const int quarter = warp & 3;               // TMEM lanes 32 quarter .. (warp % 4 rule)
     const int r = 32 * quarter + lane;          // tile row
-    const bool leader = warp == 2 + 4 * eg && lane == 0;
+    const bool leader = warp == kEpiWarp0 + 4 * eg && lane == 0;
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16);
-    unsigned char *a2 = smem + kOffA2 + eg * kA2Bytes;
-    const uint32_t sa2 = smem_u32(a2);
-    const uint32_t c1 = 128 * eg, c2 = 128 * eg + 64, c3 = c2;  // layer 1, 2, 3 columns
+    const float *pop = reinterpret_cast<const float *>(smem + kOffPop + eg * kPopBytes) + r;
+    const uint32_t spop = smem_u32(pop);
+    // columns: c1 the layer-1 accumulator, then the BF16 rows h1 and h2 (A
+    // operands of layers 2 and 3) in its first 32 columns; c2 layer 2, then 3
+    const uint32_t c1 = 128 * eg, c2 = 128 * eg + 64, c3 = c2;
+    const uint32_t tpr = (uint32_t)g.nx / kCRows;
     uint32_t ph2 = 0, ph3 = 0;
     int j = eg;  // the block's tile index
     for (long long tile = blockIdx.x + (long long)eg * gridDim.x; tile < ntiles;
          tile += (long long)kGroups * gridDim.x, j += kGroups) {
+      // this row's cell; its 27 populations go to shared memory while the
+      // network runs (each cell reads only locations no other cell touches)
+      const uint32_t t = (uint32_t)tile, row = t / tpr;
+      const int x = (int)(t - row * tpr) * kCRows + r;
+      const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
+#pragma unroll
+      for (int i = 0; i < 27; ++i)
+        cp_async4(spop + i * kCRows * 4, f + closure_read_offset<PARITY, IDX>(g, x, y, z, i));
+      cp_async_commit();
       bool ok = mbar_wait(bar(kBarAcc1F + eg), (j / kGroups) & 1, lim);
       if (group_any(eg, !ok || *abort_flag)) {
         *abort_flag = 1;
@@ -311,23 +362,21 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       fence_after();
       uint32_t v[32];
       float *trace_row = TRACE ? trace + ((long long)tile * kCRows + r) * kConvTrace : nullptr;
-      // layer 1 epilogue (hidden row 1), releasing the accumulator once read
+      // layer 1 epilogue: h1 over the accumulator columns already read
       load_acc32(lane_addr + c1, v);
-      hidden_half<TRACE>(v, sb, 0, a2, r, trace_row);
+      hidden_tmem<TRACE>(v, sb, 0, lane_addr + c1, trace_row);
       load_acc32(lane_addr + c1 + 32, v);
+      hidden_tmem<TRACE>(v, sb, 32, lane_addr + c1 + 16, trace_row);
+      tmem_wait_st();
       fence_before();
-      group_sync(eg);
-      if (leader) mbar_arrive(bar(kBarAcc1E + eg));
-      hidden_half<TRACE>(v, sb, 32, a2, r, trace_row);
-      fence_async_smem();
       group_sync(eg);
       if (leader) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-          umma(tmem + c2, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
-               sdesc(sw2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
-               idesc_bf16(kCRows, kMlpHidden), ks > 0);
+          umma_ts(tmem + c2, tmem + c1 + 8 * ks,
+                  sdesc(sw2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
+                  idesc_bf16(kCRows, kMlpHidden), ks > 0);
         umma_commit(bar(kBarL2 + eg));
       }
       ok = mbar_wait(bar(kBarL2 + eg), ph2, lim);
@@ -337,21 +386,23 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         break;
       }
       fence_after();
-      // layer 2 epilogue (hidden row 2 over row 1, which layer 2 has read)
+      // layer 2 epilogue: h2 over h1, which layer 2 has read
       load_acc32(lane_addr + c2, v);
-      hidden_half<TRACE>(v, sb + kMlpHidden, 0, a2, r, TRACE ? trace_row + kMlpHidden : nullptr);
+      hidden_tmem<TRACE>(v, sb + kMlpHidden, 0, lane_addr + c1,
+                         TRACE ? trace_row + kMlpHidden : nullptr);
       load_acc32(lane_addr + c2 + 32, v);
-      hidden_half<TRACE>(v, sb + kMlpHidden, 32, a2, r, TRACE ? trace_row + kMlpHidden : nullptr);
-      fence_async_smem();
+      hidden_tmem<TRACE>(v, sb + kMlpHidden, 32, lane_addr + c1 + 16,
+                         TRACE ? trace_row + kMlpHidden : nullptr);
+      tmem_wait_st();
       fence_before();
       group_sync(eg);
       if (leader) {
         fence_after();
 #pragma unroll
         for (int ks = 0; ks < kMlpHidden / 16; ++ks)
-          umma(tmem + c3, sdesc(sa2 + 256 * ks, 128, (kMlpHidden / 8) * 128),
-               sdesc(sw3 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(kCRows, kMlpOut),
-               ks > 0);
+          umma_ts(tmem + c3, tmem + c1 + 8 * ks,
+                  sdesc(sw3 + 256 * ks, 128, (kMlpHidden / 8) * 128), idesc_bf16(kCRows, kMlpOut),
+                  ks > 0);
         umma_commit(bar(kBarL3 + eg));
       }
       ok = mbar_wait(bar(kBarL3 + eg), ph3, lim);
@@ -361,6 +412,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         break;
       }
       fence_after();
+      // layer 3 has read h2: the first 64 columns go back to the layer-1 MMAs
+      if (leader) mbar_arrive(bar(kBarAcc1E + eg));
       load_acc32(lane_addr + c3, v);
       fence_before();
       // the closure update of this row's cell with its 17 predictions
@@ -371,13 +424,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       if (TRACE)
 #pragma unroll
         for (int k = 0; k < kMlpOutUsed; ++k) trace_row[2 * kMlpHidden + k] = yk[k];
-      const uint32_t t = (uint32_t)tile, tpr = (uint32_t)g.nx / kCRows;
-      const uint32_t row = t / tpr;
-      const int x = (int)(t - row * tpr) * kCRows + r;
-      closure_update_cell<PARITY, IDX>(p, f, g, om1, x, (int)(row % (uint32_t)g.ny),
-                                       (int)(row / (uint32_t)g.ny), yk, fallbacks, bound,
-                                       dead_zone);
+      cp_async_wait_all();
+      float df[27];
+#pragma unroll
+      for (int i = 0; i < 27; ++i) df[i] = pop[i * kCRows];
+      closure_update_cell_df<PARITY, IDX>(p, f, g, om1, x, y, z, df, yk, fallbacks, bound,
+                                          dead_zone);
     }
+    cp_async_wait_all();  // no copy into shared memory outlives the block
   }
 
   __syncthreads();
@@ -385,12 +439,15 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     // copies and MMAs still in flight land before the memory goes away
     if (tid == 0) {
       atomicExch(status, 1);
-      for (int k = counts[1]; k < counts[0]; ++k)
-        mbar_wait(bar(kBarFull + k % kStages), (k / kStages) & 1);
+      // the loads no issuer has seen land (issuer i saw its first counts[1 + i]
+      // tiles; a stage holds at most one unseen load)
+      for (int k = 0; k < counts[0]; ++k)
+        if (k >= k % kIssuers + kIssuers * counts[1 + k % kIssuers])
+          mbar_wait(bar(kBarFull + k % kStages), (k / kStages) & 1);
     }
-    const bool lead = warp >= 2 && ((warp - 2) & 3) == 0 && lane == 0;
-    if ((warp == 1 && lane == 0) || lead) {
-      const int d = warp == 1 ? 0 : 1 + ((warp - 2) >> 2);
+    const bool lead = warp >= kEpiWarp0 && ((warp - kEpiWarp0) & 3) == 0 && lane == 0;
+    if ((warp >= 1 && warp <= kIssuers && lane == 0) || lead) {
+      const int d = warp <= kIssuers ? warp - 1 : kIssuers + ((warp - kEpiWarp0) >> 2);
       umma_commit(bar(kBarDrain + d));
       mbar_wait(bar(kBarDrain + d), 0);
     }
@@ -404,32 +461,63 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                  : "memory");
 }
 
-// Feature source: standardised moments (BF16, 16 channels) of every cell of
-// the periodically padded grid, from the logical populations of an FP32 store.
-// The same moments and rounding as the features of lb_closure_features.
-__global__ void __launch_bounds__(256)
+// Feature source: standardised moments (BF16) of every position of the
+// periodically padded grid, from the logical populations of an FP32 store,
+// in the two halves described at the top of this file. The same moments and
+// rounding as the features of lb_closure_features. A block of 256 threads
+// computes 256 consecutive positions (x fastest) and writes the 254 inner
+// ones, so that half 1 takes moments 8 and 9 of the neighbours at X - 1 and
+// X + 1 from shared memory (for X = 0 and X = nx + 1, whose half 1 no tile
+// reads, they come from the neighbouring rows).
+constexpr int kFsThreads = 256, kFsOut = kFsThreads - 2;
+
+__global__ void __launch_bounds__(kFsThreads)
     feature_source_kernel(MlpDevice p, const float *__restrict__ f, const Grid g, const int parity,
                           uint4 *__restrict__ xs) {
+  __shared__ uint32_t s89[kFsThreads];
+  const long long px = g.nx + 2, py = g.ny + 2, pz = g.nz + 2, total = px * py * pz;
+  const long long q = (long long)blockIdx.x * kFsOut + threadIdx.x - 1;
+  const bool valid = q >= 0 && q < total;
+  uint32_t w[5] = {0u, 0u, 0u, 0u, 0u};
+  long long row = 0;
+  int X = 0;
+  if (valid) {
+    X = (int)(q % px);
+    row = q / px;
+    const int Yp = (int)(row % py), Z = (int)(row / py);
+    const int x = X == 0 ? g.nx - 1 : (X == g.nx + 1 ? 0 : X - 1);
+    const int y = Yp == 0 ? g.ny - 1 : (Yp == g.ny + 1 ? 0 : Yp - 1);
+    const int z = Z == 0 ? g.nz - 1 : (Z == g.nz + 1 ? 0 : Z - 1);
+    float df[27];
+    load_logical<27, 0>(f, g, parity, x, y, z, df);
+    const Macro m = Lattice<27>::moments(df);
+    const float v[kMlpMoments] = {m.drho, m.ux,  m.uy,  m.uz,  m.pxx,
+                                  m.pxy,  m.pxz, m.pyy, m.pyz, m.pzz};
+#pragma unroll
+    for (int k = 0; k < kMlpMoments; k += 2)
+      w[k / 2] = pack_bf16((v[k] - p.in_mean[k]) * p.in_inv_std[k],
+                           (v[k + 1] - p.in_mean[k + 1]) * p.in_inv_std[k + 1]);
+  }
+  s89[threadIdx.x] = w[4];
+  __syncthreads();
+  if (valid && threadIdx.x >= 1 && threadIdx.x <= kFsOut) {
+    const long long o = row * (g.nx + kPadPos) + X;
+    xs[o] = make_uint4(w[0], w[1], w[2], w[3]);
+    xs[(long long)pz * py * (g.nx + kPadPos) + o] =
+        make_uint4(s89[threadIdx.x - 1], w[4], s89[threadIdx.x + 1], 0u);
+  }
+}
+
+// The feature source in the channels-last form of lb_closure_step_trace:
+// out[position][16], channels 0..9 the moments, 10..15 zero.
+__global__ void __launch_bounds__(256)
+    export_features_kernel(const uint4 *__restrict__ xs, const Grid g, uint4 *__restrict__ out) {
   const long long px = g.nx + 2, py = g.ny + 2, pz = g.nz + 2;
   const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
   if (q >= px * py * pz) return;
-  const int X = (int)(q % px);
-  const long long t = q / px;
-  const int Yp = (int)(t % py), Z = (int)(t / py);
-  const int x = X == 0 ? g.nx - 1 : (X == g.nx + 1 ? 0 : X - 1);
-  const int y = Yp == 0 ? g.ny - 1 : (Yp == g.ny + 1 ? 0 : Yp - 1);
-  const int z = Z == 0 ? g.nz - 1 : (Z == g.nz + 1 ? 0 : Z - 1);
-  float df[27];
-  load_logical<27, 0>(f, g, parity, x, y, z, df);
-  const Macro m = Lattice<27>::moments(df);
-  const float v[kMlpMoments] = {m.drho, m.ux, m.uy, m.uz, m.pxx, m.pxy, m.pxz, m.pyy, m.pyz, m.pzz};
-  uint32_t w[5];
-#pragma unroll
-  for (int k = 0; k < kMlpMoments; k += 2)
-    w[k / 2] = pack_bf16((v[k] - p.in_mean[k]) * p.in_inv_std[k],
-                         (v[k + 1] - p.in_mean[k + 1]) * p.in_inv_std[k + 1]);
-  xs[2 * q] = make_uint4(w[0], w[1], w[2], w[3]);
-  xs[2 * q + 1] = make_uint4(w[4], 0u, 0u, 0u);
+  const long long o = (q / px) * (g.nx + kPadPos) + q % px;
+  out[2 * q] = xs[o];
+  out[2 * q + 1] = make_uint4(xs[pz * py * (g.nx + kPadPos) + o].y, 0u, 0u, 0u);
 }
 
 }  // namespace
@@ -437,7 +525,7 @@ __global__ void __launch_bounds__(256)
 bool mlp_conv_supported(const Grid &g) { return g.nx % kCRows == 0 && g.walls == 0; }
 
 size_t feature_source_bytes(const Grid &g) {
-  return (size_t)(g.nx + 2) * (size_t)(g.ny + 2) * (size_t)(g.nz + 2) * 32;
+  return 2 * (size_t)(g.nx + kPadPos) * (size_t)(g.ny + 2) * (size_t)(g.nz + 2) * 16;
 }
 
 cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map) {
@@ -450,12 +538,14 @@ cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map) {
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[4] = {16, (cuuint64_t)g.nx + 2, (cuuint64_t)g.ny + 2,
-                              (cuuint64_t)g.nz + 2};
-  const cuuint64_t strides[3] = {32, 32 * dims[1], 32 * dims[1] * dims[2]};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kCSpan, 1, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, xs, dims, strides, box,
+  // [half][Z][Y][chunk][8 positions x 8 channels]
+  const cuuint64_t rowb = (cuuint64_t)(g.nx + kPadPos) * 16;
+  const cuuint64_t dims[5] = {8 * kChunk, (cuuint64_t)(g.nx + kPadPos) / kChunk,
+                              (cuuint64_t)g.ny + 2, (cuuint64_t)g.nz + 2, 2};
+  const cuuint64_t strides[4] = {16 * kChunk, rowb, rowb * dims[2], rowb * dims[2] * dims[3]};
+  const cuuint32_t box[5] = {8 * kChunk, kRowPos / kChunk, 3, 3, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xs, dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
@@ -464,8 +554,15 @@ cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map) {
 cudaError_t launch_feature_source(const MlpDevice &p, const float *f, const Grid &g, int parity,
                                   void *xs, cudaStream_t st) {
   const long long cells = (long long)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
-  feature_source_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(
+  feature_source_kernel<<<(unsigned)((cells + kFsOut - 1) / kFsOut), kFsThreads, 0, st>>>(
       p, f, g, parity, static_cast<uint4 *>(xs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_features(const void *xs, const Grid &g, void *out, cudaStream_t st) {
+  const long long cells = (long long)(g.nx + 2) * (g.ny + 2) * (g.nz + 2);
+  export_features_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(
+      static_cast<const uint4 *>(xs), g, static_cast<uint4 *>(out));
   return cudaGetLastError();
 }
 

@@ -460,8 +460,8 @@ def test_fused_closure_step_layer_by_layer(shape):
     """The fused closure update, each stage against the FP64 reference with a
     tight bound (the inspection form lb_closure_step_trace returns what the
     kernels computed): the feature source is the BF16 rounding of the
-    standardised moments of every cell and halo position; the 27-tap
-    convolution, the hidden layer and the output layer follow the network
+    standardised moments of every cell and halo position; the convolution
+    (18 MMAs of K = 16 over the 270 features), the hidden layer and the output layer follow the network
     checks above from those features; the corrected update from the kernel's
     predictions (shrunk by the dead zone) matches the reference collision and
     streaming to FP32 precision."""
@@ -496,7 +496,7 @@ def test_fused_closure_step_layer_by_layer(shape):
         X[:, 10 * nb:10 * nb + 10] = blk.reshape(10, -1).T
     Y = np.zeros((X.shape[0], 32))
     Y[:, :17] = tr[:, 128:145]
-    check_forward_chain(X, p, tr[:, :64], tr[:, 64:128], Y, k1=27 * 16)
+    check_forward_chain(X, p, tr[:, :64], tr[:, 64:128], Y)
     # the update from the kernel's predictions
     yd = np.sign(Y[:, :17]) * np.maximum(np.abs(Y[:, :17]) - theta, 0.0)
     assert np.count_nonzero(yd) > 0.1 * yd.size  # the dead zone leaves a correction
