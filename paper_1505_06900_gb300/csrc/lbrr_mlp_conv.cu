@@ -11,9 +11,9 @@
 //   half 0: moments 0..7 (rho - 1, ux, uy, uz, Pi xx, xy, xz, yy) at X;
 //   half 1: moments 8, 9 (Pi yz, zz) at X - 1, X and X + 1, then two zeros.
 // For a tile of 128 cells x0 .. x0 + 127 of row (y, z) the producer copies,
-// per half, the 3 x 3 neighbour rows Y = y .. y + 2, Z = z .. z + 2 over the
-// positions X = x0 .. x0 + 135 in one TMA tile load whose rows are 128-byte
-// chunks of 8 positions. In shared memory each neighbour row is then
+// per half and per z plane Z = z .. z + 2, the 3 neighbour rows Y = y .. y + 2
+// over the positions X = x0 .. x0 + 135 in one TMA tile load whose rows are
+// 128-byte chunks of 8 positions. In shared memory each neighbour row is then
 // [136 positions][16 bytes]: the canonical K-major layout without swizzle
 // (8-row groups 128 bytes apart) with position X = x0 + r at row r, so that
 // a cell's neighbour at dx is row m + dx + 1 of its tile row m. Layer 1 is
@@ -24,10 +24,14 @@
 // of all three dx. The weight operand of each MMA is W1's 16 matching
 // columns.
 //
-// One persistent block per SM, eighteen warps:
-//   warp 0      TMA producer: 2 tile loads per tile into one of 2 stages
-//   warp 1      layer-1 MMA issuer (and TMEM owner)
-//   warps 2-17  four epilogue groups of four warps taking every fourth tile;
+// One persistent block per SM, nineteen warps:
+//   warp 0      TMA producer: per tile 2 tile loads (halves) for each of the 3 z
+//               planes of one of 2 stages; a plane has its own full / empty
+//               barriers, so the next tile's first plane loads while the MMAs
+//               still read the later planes of this one
+//   warps 1, 2  layer-1 MMA issuers of alternate tiles (warp 1 owns the TMEM),
+//               so that one waits for its next plane while the other issues
+//   warps 3-18  four epilogue groups of four warps taking every fourth tile;
 //               thread = TMEM lane = tile row. When a group starts a tile,
 //               each thread sends the 27 populations its cell's update reads
 //               to shared memory (cp.async). The group then reads its layer-1
@@ -71,15 +75,17 @@ constexpr int kPadPos = 8;                          // padded row: nx + 8 positi
 constexpr uint32_t kRowBytes = kRowPos * 16;        // one neighbour row of one half
 constexpr uint32_t kHalfBytes = 9 * kRowBytes;      // the 9 neighbour rows of one half
 constexpr uint32_t kStageBytes = 2 * kHalfBytes;
-constexpr uint32_t kTxBytes = kStageBytes;          // bytes a stage receives
 constexpr int kStages = 2;
+constexpr int kParts = 3;                           // z planes of a stage, each with its barriers
+constexpr int kPartRows = 9 / kParts;               // neighbour rows of a part (per half)
+constexpr uint32_t kTxPart = 2 * kPartRows * kRowBytes;  // bytes a part receives
 constexpr int kMmas1 = 18;                          // layer-1 MMAs, K = 16 each
 constexpr uint32_t kW1Bytes = 2 * kMlpHidden * 16;  // W1 block of one layer-1 MMA
 static_assert(kRowPos % kChunk == 0 && kRowPos >= kCRows + 2, "staged row covers the taps");
 static_assert(kPadPos % kChunk == 0 && kPadPos >= kRowPos - kCRows, "last box inside the row");
 constexpr uint32_t kPopBytes = 27 * kCRows * 4;    // populations of one tile, [27][128]
 constexpr int kGroups = 4;                          // epilogue groups
-constexpr int kIssuers = 1;                         // layer-1 MMA warps
+constexpr int kIssuers = 2;                         // layer-1 MMA warps
 constexpr int kEpiWarp0 = 1 + kIssuers;             // first warp of the epilogue groups
 constexpr int kConvThreads = 32 * (kEpiWarp0 + 4 * kGroups);
 constexpr uint32_t kTmemCols = 512;
@@ -90,23 +96,24 @@ constexpr uint32_t kOffW3 = kOffW2 + kMlpHidden * kMlpHidden * 2;
 constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
 constexpr uint32_t kOffPop = kOffA1 + kStages * kStageBytes;
 constexpr uint32_t kOffMisc = kOffPop + kGroups * kPopBytes;
-constexpr uint32_t kConvSmem = kOffMisc + 1024;
+constexpr uint32_t kOffBias = 512;                   // biases, after barriers and counters
+constexpr uint32_t kConvSmem = kOffMisc + kOffBias + 4 * (2 * kMlpHidden + kMlpOut);
 static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfBytes % 128 == 0,
               "TMA destinations are 128-byte aligned");
 static_assert(kConvSmem <= 232448, "fits the shared memory of one block");
 
 // mbarriers in the misc area
 enum : int {
-  kBarFull = 0,                       // [stages] stage loaded (TMA transaction bytes)
-  kBarEmpty = kBarFull + kStages,     // [stages] stage consumed by the layer-1 MMAs
-  kBarAcc1F = kBarEmpty + kStages,    // [groups] layer-1 accumulator ready (tcgen05.commit)
+  kBarFull = 0,                       // [stages x parts] part loaded (TMA transaction bytes)
+  kBarEmpty = kBarFull + kStages * kParts,  // [stages x parts] part read by the layer-1 MMAs
+  kBarAcc1F = kBarEmpty + kStages * kParts,  // [groups] layer-1 accumulator ready (commit)
   kBarAcc1E = kBarAcc1F + kGroups,    // [groups] layer-1 accumulator read by its group
   kBarL2 = kBarAcc1E + kGroups,       // [groups] layer 2 done
   kBarL3 = kBarL2 + kGroups,          // [groups] layer 3 done
   kBarDrain = kBarL3 + kGroups,       // [issuers + groups] drain of each MMA issuer after an abort
   kNumBars = kBarDrain + kIssuers + kGroups
 };
-static_assert(kNumBars * 8 + 8 + 4 * (1 + kIssuers) <= 256,
+static_assert(kNumBars * 8 + 8 + 4 * (1 + kIssuers) <= kOffBias,
               "barriers, TMEM slot, abort flag and counters before the biases");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
@@ -191,8 +198,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffMisc);
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kOffMisc + kNumBars * 8);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-  int *counts = reinterpret_cast<int *>(tmem_slot + 2);  // loads issued, landed per issuer
-  float *sb = reinterpret_cast<float *>(smem + kOffMisc + 256);  // b1, b2, b3
+  int *counts = reinterpret_cast<int *>(tmem_slot + 2);  // parts issued, seen per issuer
+  float *sb = reinterpret_cast<float *>(smem + kOffMisc + kOffBias);  // b1, b2, b3
   auto bar = [&](int k) -> uint32_t { return smem_u32(bars + k); };
 
   // ---- weights (canonical layouts) and biases
@@ -262,27 +269,31 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];\n" ::"l"(reinterpret_cast<uint64_t>(&xs_map))
                    : "memory");
-      int issued = 0;
-      for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        if (*abort_flag) break;
-        const int s = issued % kStages, use = issued / kStages;
-        if (!mbar_wait(bar(kBarEmpty + s), (use & 1) ^ 1, lim)) {
-          *abort_flag = 1;
-          break;
-        }
-        mbar_expect_tx(bar(kBarFull + s), kTxBytes);
+      int issued = 0;  // parts
+      bool stop = false;
+      for (long long tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+        const int j = issued / kParts, s = j % kStages, use = j / kStages;
         // tile -> (x0, y, z) in 32-bit arithmetic (the launcher keeps the
         // tile count below 2^31)
         const uint32_t t = (uint32_t)tile, tpr = (uint32_t)g.nx / kCRows;
         const uint32_t row = t / tpr;
         const int x0 = (int)(t - row * tpr) * kCRows;
         const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-        // padded rows Y = y .. y + 2, Z = z .. z + 2, chunks from X = x0
+        // part k: padded rows Y = y .. y + 2, Z = z + k kPartRows .., chunks from X = x0
+        for (int k = 0; k < kParts; ++k) {
+          const int b = s * kParts + k;
+          if (*abort_flag || !mbar_wait(bar(kBarEmpty + b), (use & 1) ^ 1, lim)) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          mbar_expect_tx(bar(kBarFull + b), kTxPart);
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-          tma_load_5d(sa1 + s * kStageBytes + h * kHalfBytes, &xs_map, 0, x0 / kChunk, y, z, h,
-                      bar(kBarFull + s));
-        ++issued;
+          for (int h = 0; h < 2; ++h)
+            tma_load_5d(sa1 + s * kStageBytes + h * kHalfBytes + k * kPartRows * kRowBytes,
+                        &xs_map, 0, x0 / kChunk, y, z + k * (3 / kParts), h, bar(kBarFull + b));
+          ++issued;
+        }
       }
       counts[0] = issued;
     }
@@ -291,21 +302,15 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     // warp 1 + i takes the tiles j = i mod kIssuers (stage j mod kStages)
     if (lane == 0) {
       const int iw = warp - 1;
-      int landed = 0;
-      for (long long tile = blockIdx.x + (long long)iw * gridDim.x; tile < ntiles;
-           tile += (long long)kIssuers * gridDim.x) {
-        if (*abort_flag) break;
-        const int j = iw + kIssuers * landed, s = j % kStages, gs = j % kGroups;
-        if (!mbar_wait(bar(kBarFull + s), (j / kStages) & 1, lim)) {
+      int landed = 0, nt = 0;  // parts seen, tiles started
+      bool stop = false;
+      for (long long tile = blockIdx.x + (long long)iw * gridDim.x; tile < ntiles && !stop;
+           tile += (long long)kIssuers * gridDim.x, ++nt) {
+        const int j = iw + kIssuers * nt, s = j % kStages, gs = j % kGroups;
+        if (*abort_flag || !mbar_wait(bar(kBarAcc1E + gs), ((j / kGroups) & 1) ^ 1, lim)) {
           *abort_flag = 1;
           break;
         }
-        ++landed;
-        if (!mbar_wait(bar(kBarAcc1E + gs), ((j / kGroups) & 1) ^ 1, lim)) {
-          *abort_flag = 1;
-          break;
-        }
-        fence_after();
         // descriptors of neighbour row 0; a row adds its byte offset / 16 to
         // the start address field (no carry: shared addresses stay below
         // 256 KB). aP: rows m, m + 1 of half 0 (dx = -1, 0); aQ: row m + 2 of
@@ -316,15 +321,26 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         const uint64_t b0 = sdesc(sw1, 1024, 128);
         const uint32_t d = tmem + 128 * gs;
 #pragma unroll
-        for (int r9 = 0; r9 < 9; ++r9) {
-          const uint32_t ro = (r9 * kRowBytes) >> 4;
-          umma(d, aP + ro, b0 + ((2 * r9 * kW1Bytes) >> 4), idesc_bf16(kCRows, kMlpHidden),
-               r9 > 0);
-          umma(d, aQ + ro, b0 + (((2 * r9 + 1) * kW1Bytes) >> 4),
-               idesc_bf16(kCRows, kMlpHidden), 1);
+        for (int k = 0; k < kParts; ++k) {
+          const int b = s * kParts + k;
+          if (!mbar_wait(bar(kBarFull + b), (j / kStages) & 1, lim)) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          ++landed;
+          fence_after();
+#pragma unroll
+          for (int r9 = k * kPartRows; r9 < (k + 1) * kPartRows; ++r9) {
+            const uint32_t ro = (r9 * kRowBytes) >> 4;
+            umma(d, aP + ro, b0 + ((2 * r9 * kW1Bytes) >> 4), idesc_bf16(kCRows, kMlpHidden),
+                 r9 > 0);
+            umma(d, aQ + ro, b0 + (((2 * r9 + 1) * kW1Bytes) >> 4),
+                 idesc_bf16(kCRows, kMlpHidden), 1);
+          }
+          umma_commit(bar(kBarEmpty + b));  // the part may be refilled once these are done
         }
-        umma_commit(bar(kBarEmpty + s));
-        umma_commit(bar(kBarAcc1F + gs));
+        if (!stop) umma_commit(bar(kBarAcc1F + gs));
       }
       counts[1 + iw] = landed;
     }
@@ -439,11 +455,13 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     // copies and MMAs still in flight land before the memory goes away
     if (tid == 0) {
       atomicExch(status, 1);
-      // the loads no issuer has seen land (issuer i saw its first counts[1 + i]
-      // tiles; a stage holds at most one unseen load)
-      for (int k = 0; k < counts[0]; ++k)
-        if (k >= k % kIssuers + kIssuers * counts[1 + k % kIssuers])
-          mbar_wait(bar(kBarFull + k % kStages), (k / kStages) & 1);
+      // the parts no issuer has seen land (issuer i saw the first counts[1 + i]
+      // parts of its tiles; a part of a stage holds at most one unseen load)
+      for (int q = 0; q < counts[0]; ++q) {
+        const int j = q / kParts, k = q % kParts, i = j % kIssuers;
+        if (kParts * (j / kIssuers) + k >= counts[1 + i])
+          mbar_wait(bar(kBarFull + (j % kStages) * kParts + k), (j / kStages) & 1);
+      }
     }
     const bool lead = warp >= kEpiWarp0 && ((warp - kEpiWarp0) & 3) == 0 && lane == 0;
     if ((warp >= 1 && warp <= kIssuers && lane == 0) || lead) {
@@ -543,7 +561,7 @@ cudaError_t make_feature_map(void *xs, const Grid &g, CUtensorMap *map) {
   const cuuint64_t dims[5] = {8 * kChunk, (cuuint64_t)(g.nx + kPadPos) / kChunk,
                               (cuuint64_t)g.ny + 2, (cuuint64_t)g.nz + 2, 2};
   const cuuint64_t strides[4] = {16 * kChunk, rowb, rowb * dims[2], rowb * dims[2] * dims[3]};
-  const cuuint32_t box[5] = {8 * kChunk, kRowPos / kChunk, 3, 3, 1};
+  const cuuint32_t box[5] = {8 * kChunk, kRowPos / kChunk, 3, 3 / kParts, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, xs, dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
