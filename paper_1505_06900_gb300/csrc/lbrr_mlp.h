@@ -75,11 +75,13 @@ __device__ __forceinline__ IDX closure_read_offset(const Grid &g, int x, int y, 
 // the standardised prediction y = ystd[k] shrunk by the dead zone; plain RR
 // for the cell (counted in *fallbacks) when a standardised prediction exceeds
 // the bound (or is not a number) or a corrected population is not positive.
-// Each cell writes exactly the locations it reads.
+// Each cell writes exactly the locations it reads. out_scale: the 17
+// scales (device or shared memory).
 template <int PARITY, typename IDX = long long>
-__device__ __forceinline__ void closure_update_cell_df(const MlpDevice &p, float *__restrict__ f,
-                                                       const Grid &g, const float om1, int x,
-                                                       int y, int z, const float (&df)[27],
+__device__ __forceinline__ void closure_update_cell_df(const float *out_scale,
+                                                       float *__restrict__ f, const Grid &g,
+                                                       const float om1, int x, int y, int z,
+                                                       const float (&df)[27],
                                                        const float (&ystd)[kMlpOutUsed],
                                                        unsigned long long *fallbacks,
                                                        const float bound, const float dead_zone) {
@@ -92,13 +94,15 @@ __device__ __forceinline__ void closure_update_cell_df(const MlpDevice &p, float
     const float yk = ystd[k];
     use = use && (fabsf(yk) <= bound);  // also false for NaN
     const float yd = copysignf(fmaxf(fabsf(yk) - dead_zone, 0.0f), yk);
-    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yd * p.out_scale[k]);
+    cc[hi_pow(k, 0)][hi_pow(k, 1)][hi_pow(k, 2)] += om1 * (yd * out_scale[k]);
   }
   float out[27];
   if (use) {
     synth_tensor_d3q27<false>(cc, out);
 #pragma unroll
-    for (int i = 0; i < 27; ++i) use = use && (out[i] + weight<3>(i) > 0.0f);
+    // f_i = out[i] + w_i > 0, compared as out[i] > -w_i: the same test, since
+    // near the boundary the sum of the two is exact (Sterbenz)
+    for (int i = 0; i < 27; ++i) use = use && (out[i] > -weight<3>(i));
   }
   if (!use) {  // plain RR: the coefficients again from the moments (rare)
     coeffs_rr_d3q27(m, om1, cc);
@@ -132,8 +136,8 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
   float df[27];
 #pragma unroll
   for (int i = 0; i < 27; ++i) df[i] = f[closure_read_offset<PARITY, IDX>(g, x, y, z, i)];
-  closure_update_cell_df<PARITY, IDX>(p, f, g, om1, x, y, z, df, ystd, fallbacks, bound,
-                                      dead_zone);
+  closure_update_cell_df<PARITY, IDX>(p.out_scale, f, g, om1, x, y, z, df, ystd, fallbacks,
+                                      bound, dead_zone);
 }
 
 size_t mlp_train_smem();

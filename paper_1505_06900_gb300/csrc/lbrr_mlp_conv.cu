@@ -9,7 +9,8 @@
 // split in two halves of 8 channels, each half laid out [Z][Y][X][8] with
 // rows padded to nx + 8 positions:
 //   half 0: moments 0..7 (rho - 1, ux, uy, uz, Pi xx, xy, xz, yy) at X;
-//   half 1: moments 8, 9 (Pi yz, zz) at X - 1, X and X + 1, then two zeros.
+//   half 1: moments 8, 9 (Pi yz, zz) at X - 1, X and X + 1, then two ones
+//           (the constant input through which layer 1 adds its bias).
 // For a tile of 128 cells x0 .. x0 + 127 of row (y, z) the producer copies,
 // per half and per z plane Z = z .. z + 2, the 3 neighbour rows Y = y .. y + 2
 // over the positions X = x0 .. x0 + 135 in one TMA tile load whose rows are
@@ -22,7 +23,8 @@
 // descriptor: (half 0 at dx = -1, half 0 at dx = 0), 16 bytes apart, and
 // (half 0 at dx = +1, half 1 at dx = 0), the latter holding moments 8 and 9
 // of all three dx. The weight operand of each MMA is W1's 16 matching
-// columns.
+// columns; at the centre row the two constant inputs meet b1 split into
+// BF16 b_hi + b_lo (b1 - b_hi - b_lo is below 2^-18 |b1|).
 //
 // One persistent block per SM, nineteen warps:
 //   warp 0      TMA producer: per tile 2 tile loads (halves) for each of the 3 z
@@ -97,7 +99,9 @@ constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
 constexpr uint32_t kOffPop = kOffA1 + kStages * kStageBytes;
 constexpr uint32_t kOffMisc = kOffPop + kGroups * kPopBytes;
 constexpr uint32_t kOffBias = 512;                   // biases, after barriers and counters
-constexpr uint32_t kConvSmem = kOffMisc + kOffBias + 4 * (2 * kMlpHidden + kMlpOut);
+// b1 (not read: layer 1 takes its bias through the constant inputs), b2,
+// b3, then the 17 output scales
+constexpr uint32_t kConvSmem = kOffMisc + kOffBias + 4 * (2 * kMlpHidden + kMlpOut + kMlpOutUsed);
 static_assert(kOffA1 % 128 == 0 && kStageBytes % 128 == 0 && kHalfBytes % 128 == 0,
               "TMA destinations are 128-byte aligned");
 static_assert(kConvSmem <= 232448, "fits the shared memory of one block");
@@ -149,21 +153,28 @@ __device__ __forceinline__ bool group_any(int g, bool pred) {
   return r != 0;
 }
 
-// tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v), rounded
-// to BF16 and packed two to a column into the 16 TMEM columns at taddr of
-// this thread's lane (the row of the next layer's A operand); with TRACE also
-// the FP32 values into trace_row[c0 ..].
-template <bool TRACE = false>
+// tanh(acc + bias) of 32 accumulator columns c0 .. c0 + 31 (in v; without
+// BIAS the accumulator holds the bias already), rounded to BF16 and packed
+// two to a column into the 16 TMEM columns at taddr of this thread's lane
+// (the row of the next layer's A operand); with TRACE also the FP32 values
+// into trace_row[c0 ..].
+template <bool TRACE = false, bool BIAS = true>
 __device__ __forceinline__ void hidden_tmem(const uint32_t (&v)[32], const float *bias, int c0,
                                             uint32_t taddr, float *trace_row = nullptr) {
   uint32_t q[16];
 #pragma unroll
   for (int k = 0; k < 32; k += 4) {
-    const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + k);
-    const float h0 = tanh_approx(__uint_as_float(v[k]) + b.x);
-    const float h1 = tanh_approx(__uint_as_float(v[k + 1]) + b.y);
-    const float h2 = tanh_approx(__uint_as_float(v[k + 2]) + b.z);
-    const float h3 = tanh_approx(__uint_as_float(v[k + 3]) + b.w);
+    float z0 = __uint_as_float(v[k]), z1 = __uint_as_float(v[k + 1]);
+    float z2 = __uint_as_float(v[k + 2]), z3 = __uint_as_float(v[k + 3]);
+    if (BIAS) {
+      const float4 b = *reinterpret_cast<const float4 *>(bias + c0 + k);
+      z0 += b.x;
+      z1 += b.y;
+      z2 += b.z;
+      z3 += b.w;
+    }
+    const float h0 = tanh_approx(z0), h1 = tanh_approx(z1);
+    const float h2 = tanh_approx(z2), h3 = tanh_approx(z3);
     if (TRACE) {
       trace_row[c0 + k] = h0;
       trace_row[c0 + k + 1] = h1;
@@ -217,11 +228,16 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       if (kind == 0 || h == 0) {  // moments 0..7 of dx = -1 / 0 (kind 0), dx = +1 (kind 1)
         nb = (kind == 0 ? h : 2) + 3 * r9;
         ch = k;
-      } else {  // moments 8, 9 of dx = -1, 0, +1, then zeros
+      } else {  // moments 8, 9 of dx = -1, 0, +1, then the constant inputs
         nb = k < 6 ? (k >> 1) + 3 * r9 : -1;
         ch = 8 + (k & 1);
       }
       w[k] = nb >= 0 ? __bfloat16_as_ushort(p.w1[n * kMlpIn + kMlpMoments * nb + ch]) : 0;
+    }
+    if (kind == 1 && h == 1 && r9 == 4) {  // b1 = b_hi + b_lo on the constant inputs
+      const __nv_bfloat16 hi = __float2bfloat16_rn(p.b1[n]);
+      w[6] = __bfloat16_as_ushort(hi);
+      w[7] = __bfloat16_as_ushort(__float2bfloat16_rn(p.b1[n] - __bfloat162float(hi)));
     }
     *reinterpret_cast<uint4 *>(smem + kOffW1 + mq * kW1Bytes + h * 1024 + n * 16) =
         make_uint4(w[0] | ((uint32_t)w[1] << 16), w[2] | ((uint32_t)w[3] << 16),
@@ -237,9 +253,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     *reinterpret_cast<uint4 *>(smem + kOffW3 + cm_offset(n, 8 * kb, kMlpHidden)) =
         *reinterpret_cast<const uint4 *>(p.w3 + n * kMlpHidden + 8 * kb);
   }
-  for (int c = tid; c < 2 * kMlpHidden + kMlpOut; c += kConvThreads)
-    sb[c] = c < kMlpHidden ? p.b1[c] : (c < 2 * kMlpHidden ? p.b2[c - kMlpHidden]
-                                                           : p.b3[c - 2 * kMlpHidden]);
+  for (int c = tid; c < 2 * kMlpHidden + kMlpOut + kMlpOutUsed; c += kConvThreads)
+    sb[c] = c < kMlpHidden ? p.b1[c]
+            : c < 2 * kMlpHidden ? p.b2[c - kMlpHidden]
+            : c < 2 * kMlpHidden + kMlpOut ? p.b3[c - 2 * kMlpHidden]
+                                           : p.out_scale[c - 2 * kMlpHidden - kMlpOut];
   if (tid == 0) {
     for (int k = 0; k < kNumBars; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar(k)) : "memory");
@@ -380,9 +398,9 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       float *trace_row = TRACE ? trace + ((long long)tile * kCRows + r) * kConvTrace : nullptr;
       // layer 1 epilogue: h1 over the accumulator columns already read
       load_acc32(lane_addr + c1, v);
-      hidden_tmem<TRACE>(v, sb, 0, lane_addr + c1, trace_row);
+      hidden_tmem<TRACE, false>(v, sb, 0, lane_addr + c1, trace_row);
       load_acc32(lane_addr + c1 + 32, v);
-      hidden_tmem<TRACE>(v, sb, 32, lane_addr + c1 + 16, trace_row);
+      hidden_tmem<TRACE, false>(v, sb, 32, lane_addr + c1 + 16, trace_row);
       tmem_wait_st();
       fence_before();
       group_sync(eg);
@@ -444,8 +462,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       float df[27];
 #pragma unroll
       for (int i = 0; i < 27; ++i) df[i] = pop[i * kCRows];
-      closure_update_cell_df<PARITY, IDX>(p, f, g, om1, x, y, z, df, yk, fallbacks, bound,
-                                          dead_zone);
+      closure_update_cell_df<PARITY, IDX>(sb + 2 * kMlpHidden + kMlpOut, f, g, om1, x, y, z, df,
+                                          yk, fallbacks, bound, dead_zone);
     }
     cp_async_wait_all();  // no copy into shared memory outlives the block
   }
@@ -522,7 +540,7 @@ __global__ void __launch_bounds__(kFsThreads)
     const long long o = row * (g.nx + kPadPos) + X;
     xs[o] = make_uint4(w[0], w[1], w[2], w[3]);
     xs[(long long)pz * py * (g.nx + kPadPos) + o] =
-        make_uint4(s89[threadIdx.x - 1], w[4], s89[threadIdx.x + 1], 0u);
+        make_uint4(s89[threadIdx.x - 1], w[4], s89[threadIdx.x + 1], 0x3F803F80u);  // 1.0, 1.0
   }
 }
 
