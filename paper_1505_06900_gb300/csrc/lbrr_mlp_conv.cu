@@ -37,7 +37,7 @@
 //               thread = TMEM lane = tile row. When a group starts a tile,
 //               each thread sends the 27 populations its cell's update reads
 //               to shared memory (cp.async). The group then reads its layer-1
-//               accumulator, applies bias and tanh and stores the BF16
+//               accumulator (bias included), applies tanh and stores the BF16
 //               hidden row back into tensor memory, where layer 2 takes it
 //               as its A operand (issued by the group); the same for layer
 //               2 and layer 3. With the 17 standardised outputs of its row
