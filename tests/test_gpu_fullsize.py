@@ -184,3 +184,94 @@ def test_sampled_cells_f16_store_at_512_cubed():
         g_got = got[:, si] / w
         ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(g_ref), 2.0 ** -14))) - 10)
         assert np.all(np.abs(g_got - g_ref) <= ulp + 1e-6), smp
+
+
+def test_sampled_cells_fused_closure_at_256_cubed():
+    """The fused learned-closure update at 256^3, the coarse grid of the
+    learned form, launched as lb_step launches it (one persistent block per
+    SM), one update at each AA parity. For sampled cells (both 128-cell tiles
+    of a row at their edges, the periodic faces and random cells): the 27
+    neighbours' features the kernel read against the standardised oracle
+    moments of the state before the update (one BF16 unit), both hidden
+    activations and the 17 predictions against the FP64 network with the
+    bounds of the network tests, and the cell's 27 post-update populations,
+    where streaming puts them, against the oracle's corrected collision with
+    the kernel's predictions (1e-6 of the weights)."""
+    from oracle import closure as C
+    from paper_1505_06900_gb300 import binding as B
+    from _common import f64_state
+    from test_gpu_closure import bf16_params, check_forward_chain
+
+    n, theta, o_scale = 256, 0.3, 2e-5
+    shape = (n, n, n)
+    tau = W.taylor_green_3d_tau(n, 0.3, 1600.0)
+    rho, u = W.random_field(shape, 3, seed=81, a_rho=0.005, a_u=0.03)
+    rng = np.random.default_rng(82)
+    p = bf16_params(rng, (0.05, 0.15, 0.3))
+    cvel, w = O.lattice_tables(O.D3Q27)
+    # sampled cells: tile edges x = 0, 127, 128, 255 and neighbours, periodic faces
+    edge = [0, 1, 126, 127, 128, 129, 254, 255]
+    cells = [(x, y, z) for x in edge for y, z in ((0, 0), (255, 255), (0, 131), (77, 255))]
+    cells += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(64)]
+    xs_, ys_, zs_ = (np.array(v) for v in zip(*cells))
+    S = len(cells)
+    # the 27 neighbours of each sampled cell, neighbour nb = (dx+1) + 3(dy+1) + 9(dz+1)
+    nb_x = np.stack([(xs_ + (k % 3 - 1)) % n for k in range(27)], 1)
+    nb_y = np.stack([(ys_ + ((k // 3) % 3 - 1)) % n for k in range(27)], 1)
+    nb_z = np.stack([(zs_ + (k // 9 - 1)) % n for k in range(27)], 1)
+    net = B.MLP(C.pack(p))
+    with B.Solver(B.D3Q27, shape, tau) as s:
+        s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
+                      torch.from_numpy(u.astype(np.float32)).cuda())
+        r_d, u_d, pi_d = s.moments()
+        mom = torch.cat([(r_d - 1.0).reshape(1, -1), u_d.reshape(3, -1), pi_d.reshape(6, -1)])
+        mean = mom.double().mean(1).cpu().numpy().astype(np.float32)
+        inv = (1.0 / (mom.double().std(1) + 1e-12)).cpu().numpy().astype(np.float32)
+        del r_d, u_d, pi_d, mom
+        net.set_scaling(mean, inv, np.full(17, o_scale, np.float32))
+        s.set_closure(net, bound=1e6, dead_zone=theta)
+        m64, i64 = mean.astype(np.float64), inv.astype(np.float64)
+        o64 = np.full(17, np.float32(o_scale), np.float64)
+        for parity in (0, 1):
+            pre = s.populations()
+            nbf = pre[:, torch.from_numpy(nb_z.reshape(-1)).cuda(),
+                      torch.from_numpy(nb_y.reshape(-1)).cuda(),
+                      torch.from_numpy(nb_x.reshape(-1)).cuda()].cpu().numpy()
+            del pre
+            tr, xs = s.closure_step_trace()
+            sel = torch.from_numpy(np.asarray([(z * n + y) * n + x for x, y, z in cells])).cuda()
+            trs = tr.index_select(0, sel).cpu().numpy().astype(np.float64)
+            feat = xs[torch.from_numpy(nb_z.reshape(-1) + 1).cuda(),
+                      torch.from_numpy(nb_y.reshape(-1) + 1).cuda(),
+                      torch.from_numpy(nb_x.reshape(-1) + 1).cuda()].float().cpu().numpy()
+            del tr, xs
+            post = s.populations()
+            # features: standardised oracle moments of each neighbour, one BF16 unit
+            f_nb = f64_state(O.D3Q27, nbf.reshape(27, 1, 1, -1))
+            z_ref = (C.moment_field(f_nb).reshape(10, -1).T - m64) * i64  # [27 S, 10]
+            ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(z_ref), 1e-30))) - 7)
+            assert np.all(np.abs(feat[:, :10] - z_ref) <= ulp + 1e-5), parity
+            assert np.all(feat[:, 10:] == 0)
+            # the network, layer by layer, from the features the kernel read
+            X = np.zeros((S, 288))
+            X[:, :270] = feat[:, :10].reshape(S, 27, 10).reshape(S, 270)
+            Y = np.zeros((S, 32))
+            Y[:, :17] = trs[:, 128:145]
+            check_forward_chain(X, p, trs[:, :64], trs[:, 64:128], Y)
+            # the update: oracle collision of each cell with the kernel's predictions
+            yd = np.sign(Y[:, :17]) * np.maximum(np.abs(Y[:, :17]) - theta, 0.0)
+            assert np.count_nonzero(yd) > 0.1 * yd.size
+            f_cell = f_nb.reshape(27, S, 27)[:, :, 13]  # neighbour 13 is the cell itself
+            for c_i, (x, y, z) in enumerate(cells):
+                ref = O.collide_cell_closure(f_cell[:, c_i], tau, yd[c_i] * o64)
+                gx = (x + cvel[:, 0]) % n
+                gy = (y + cvel[:, 1]) % n
+                gz = (z + cvel[:, 2]) % n
+                got = post[torch.arange(27).cuda(), torch.from_numpy(gz).cuda(),
+                           torch.from_numpy(gy).cuda(),
+                           torch.from_numpy(gx).cuda()].cpu().numpy().astype(np.float64)
+                err = np.max(np.abs(got + w - ref) / w)
+                assert err <= 1e-6, (parity, (x, y, z), err)
+            del post
+        assert s.closure_fallbacks() == 0
+    net.close()
