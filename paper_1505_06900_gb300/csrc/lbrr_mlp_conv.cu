@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         const uint32_t row = t / tpr;
         const int x0 = (int)(t - row * tpr) * kCRows;
         const int y = (int)(row % (uint32_t)g.ny), z = (int)(row / (uint32_t)g.ny);
-        // part k: padded rows Y = y .. y + 2, Z = z + k kPartRows .., chunks from X = x0
+        // part k: the z plane Z = z + k (padded), rows Y = y .. y + 2, chunks from X = x0
         for (int k = 0; k < kParts; ++k) {
           const int b = s * kParts + k;
           if (*abort_flag || !mbar_wait(bar(kBarEmpty + b), (use & 1) ^ 1, lim)) {
