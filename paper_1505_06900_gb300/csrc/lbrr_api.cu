@@ -754,7 +754,7 @@ static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, f
   const long long tiles = (M + 63) / 64;
   const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
   cudaError_t e =
-      lbrr::launch_mlp(m->d, X, T, M, nullptr, m->gpart, m->lpart, nb, m->stream, trace);
+      lbrr::launch_mlp_train(m->d, X, T, M, m->gpart, m->lpart, nb, m->stream, trace);
   float bc1 = 1.f, bc2 = 1.f;
   if (adam) {
     const long long t = m->t + 1;

@@ -3,7 +3,8 @@
 // hidden 64 + 64, y in R^32 (17 outputs used), with the loss
 // mean((y - t)^2) over the used outputs, its backward pass and Adam.
 //
-// mlp_kernel<TRAIN> is persistent: each block walks 64-row tiles of the batch.
+// mlp_train_kernel is persistent: each block walks 64-row tiles of the batch
+// (the forward pass alone runs on the tcgen05 kernels of lbrr_mlp_tc.cu).
 // A warp owns 16 rows. Layer 1 takes its A fragments from the staged input
 // tile (ldmatrix) and its B fragments straight from the K-major BF16 weights;
 // every later layer takes the previous layer's accumulators, passed through
@@ -124,11 +125,11 @@ __device__ __forceinline__ void trace_tile(float *__restrict__ trace, long long 
   }
 }
 
-template <bool TRAIN, bool TRACE = false>
+template <bool TRACE = false>
 __global__ void __launch_bounds__(kThreads)
-    mlp_kernel(MlpDevice p, const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T,
-               long long M, float *__restrict__ Y, float *__restrict__ gpart,
-               float *__restrict__ lpart, float *__restrict__ trace) {
+    mlp_train_kernel(MlpDevice p, const __nv_bfloat16 *__restrict__ X,
+                     const float *__restrict__ T, long long M, float *__restrict__ gpart,
+                     float *__restrict__ lpart, float *__restrict__ trace) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem &s = *reinterpret_cast<TrainSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -137,12 +138,10 @@ __global__ void __launch_bounds__(kThreads)
   const long long ntiles = (M + kRows - 1) / kRows;
   const float inv_n = 1.0f / ((float)M * (float)kMlpOutUsed);
 
-  if (TRAIN) {
-    for (int k = tid; k < kMlpHidden * kMlpIn; k += kThreads) (&s.gw1[0][0])[k] = 0.f;
-    for (int k = tid; k < kMlpHidden * kMlpHidden; k += kThreads) (&s.gw2[0][0])[k] = 0.f;
-    for (int k = tid; k < kMlpOut * kMlpHidden; k += kThreads) (&s.gw3[0][0])[k] = 0.f;
-    for (int k = tid; k < 2 * kMlpHidden + kMlpOut; k += kThreads) s.gb[k] = 0.f;
-  }
+  for (int k = tid; k < kMlpHidden * kMlpIn; k += kThreads) (&s.gw1[0][0])[k] = 0.f;
+  for (int k = tid; k < kMlpHidden * kMlpHidden; k += kThreads) (&s.gw2[0][0])[k] = 0.f;
+  for (int k = tid; k < kMlpOut * kMlpHidden; k += kThreads) (&s.gw3[0][0])[k] = 0.f;
+  for (int k = tid; k < 2 * kMlpHidden + kMlpOut; k += kThreads) s.gb[k] = 0.f;
   float loss_acc = 0.f;
 
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -207,16 +206,6 @@ __global__ void __launch_bounds__(kThreads)
       y[nt][3] += p.b3[c + 1];
     }
     if (TRACE) trace_tile<4>(trace, ra, rb, M, kTraceY, t, y);
-    if (!TRAIN) {
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int c = 8 * nt + 2 * t;
-        if (ra < M) *reinterpret_cast<float2 *>(Y + ra * kMlpOut + c) = make_float2(y[nt][0], y[nt][1]);
-        if (rb < M) *reinterpret_cast<float2 *>(Y + rb * kMlpOut + c) = make_float2(y[nt][2], y[nt][3]);
-      }
-      __syncthreads();  // the input tile is reused by the next iteration
-      continue;
-    }
 
     // ---- loss and dy = 2 (y - t) / (M * 17) on the used outputs of valid rows
     float dy[4][4];
@@ -292,20 +281,18 @@ __global__ void __launch_bounds__(kThreads)
     __syncthreads();
   }
 
-  if (TRAIN) {
-    // ---- block partials in the packed parameter order
-    float *o = gpart + (long long)blockIdx.x * kMlpParams;
-    for (int k = tid; k < kMlpHidden * kMlpIn; k += kThreads) o[kOffW1 + k] = (&s.gw1[0][0])[k];
-    for (int k = tid; k < kMlpHidden; k += kThreads) o[kOffB1 + k] = s.gb[k];
-    for (int k = tid; k < kMlpHidden * kMlpHidden; k += kThreads) o[kOffW2 + k] = (&s.gw2[0][0])[k];
-    for (int k = tid; k < kMlpHidden; k += kThreads) o[kOffB2 + k] = s.gb[kMlpHidden + k];
-    for (int k = tid; k < kMlpOut * kMlpHidden; k += kThreads) o[kOffW3 + k] = (&s.gw3[0][0])[k];
-    for (int k = tid; k < kMlpOut; k += kThreads) o[kOffB3 + k] = s.gb[2 * kMlpHidden + k];
-    for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-    if (lane == 0) s.loss[warp] = loss_acc;
-    __syncthreads();
-    if (tid == 0) lpart[blockIdx.x] = ((s.loss[0] + s.loss[1]) + s.loss[2]) + s.loss[3];
-  }
+  // ---- block partials in the packed parameter order
+  float *o = gpart + (long long)blockIdx.x * kMlpParams;
+  for (int k = tid; k < kMlpHidden * kMlpIn; k += kThreads) o[kOffW1 + k] = (&s.gw1[0][0])[k];
+  for (int k = tid; k < kMlpHidden; k += kThreads) o[kOffB1 + k] = s.gb[k];
+  for (int k = tid; k < kMlpHidden * kMlpHidden; k += kThreads) o[kOffW2 + k] = (&s.gw2[0][0])[k];
+  for (int k = tid; k < kMlpHidden; k += kThreads) o[kOffB2 + k] = s.gb[kMlpHidden + k];
+  for (int k = tid; k < kMlpOut * kMlpHidden; k += kThreads) o[kOffW3 + k] = (&s.gw3[0][0])[k];
+  for (int k = tid; k < kMlpOut; k += kThreads) o[kOffB3 + k] = s.gb[2 * kMlpHidden + k];
+  for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+  if (lane == 0) s.loss[warp] = loss_acc;
+  __syncthreads();
+  if (tid == 0) lpart[blockIdx.x] = ((s.loss[0] + s.loss[1]) + s.loss[2]) + s.loss[3];
 }
 
 // Sum of the block partials (fixed order), optional Adam update of the FP32
@@ -361,16 +348,16 @@ __device__ void mlp_refresh_one(MlpDevice p, int k, float w) {
 
 size_t mlp_train_smem() { return sizeof(TrainSmem); }
 
-cudaError_t launch_mlp(const MlpDevice &p, const void *X, const float *T, long long M, float *Y,
-                       float *gpart, float *lpart, int nblocks, cudaStream_t st, float *trace) {
+cudaError_t launch_mlp_train(const MlpDevice &p, const void *X, const float *T, long long M,
+                             float *gpart, float *lpart, int nblocks, cudaStream_t st,
+                             float *trace) {
   const size_t smem = sizeof(TrainSmem);
-  const bool train = T != nullptr;
-  if (trace && !train) return cudaErrorInvalidValue;
-  auto kern = trace ? mlp_kernel<true, true> : (train ? mlp_kernel<true> : mlp_kernel<false>);
+  if (!T) return cudaErrorInvalidValue;
+  auto kern = trace ? mlp_train_kernel<true> : mlp_train_kernel<false>;
   cudaError_t e =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<nblocks, kThreads, smem, st>>>(p, static_cast<const __nv_bfloat16 *>(X), T, M, Y, gpart,
+  kern<<<nblocks, kThreads, smem, st>>>(p, static_cast<const __nv_bfloat16 *>(X), T, M, gpart,
                                        lpart, trace);
   return cudaGetLastError();
 }

@@ -149,12 +149,12 @@ size_t mlp_train_smem();
 constexpr int kTraceH1 = 0, kTraceH2 = 64, kTraceY = 128, kTraceDy = 160, kTraceDh2 = 192,
               kTraceDh1 = 256, kMlpTrace = 320;
 
-// Forward (T == nullptr: writes Y [M][32]) or forward + backward (writes the
+// Forward + backward of a batch on the warp-level tensor cores (writes the
 // block partial gradients gpart [nblocks][kMlpParams] and losses lpart); with
-// trace (backward only) also the trace rows [M][kMlpTrace].
-cudaError_t launch_mlp(const MlpDevice &p, const void *X, const float *T, long long M, float *Y,
-                       float *gpart, float *lpart, int nblocks, cudaStream_t st,
-                       float *trace = nullptr);
+// trace also the trace rows [M][kMlpTrace].
+cudaError_t launch_mlp_train(const MlpDevice &p, const void *X, const float *T, long long M,
+                             float *gpart, float *lpart, int nblocks, cudaStream_t st,
+                             float *trace = nullptr);
 // Gradient = sum of the partials; optional Adam step (bias corrections bc1,
 // bc2); loss = sum of the block losses (double, device) when loss_out != null.
 cudaError_t launch_mlp_reduce(const MlpDevice &p, const float *gpart, int nparts, float *grad_out,
