@@ -751,10 +751,10 @@ static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, f
   if (adam && !(lr > 0.f && std::isfinite(lr)))
     return mlp_fail(m, LB_EINVAL, "learning rate must be positive");
   DeviceGuard dg(m->device);
-  const long long tiles = (M + 63) / 64;
+  const long long tiles = (M + lbrr::kMlpTrainRows - 1) / lbrr::kMlpTrainRows;
   const int nb = (int)(tiles < m->nblocks ? tiles : m->nblocks);
-  cudaError_t e =
-      lbrr::launch_mlp_train(m->d, X, T, M, m->gpart, m->lpart, nb, m->stream, trace);
+  cudaError_t e = lbrr::launch_mlp_train(m->d, X, T, M, m->gpart, m->lpart, m->status, nb,
+                                         m->stream, trace);
   float bc1 = 1.f, bc2 = 1.f;
   if (adam) {
     const long long t = m->t + 1;
@@ -763,7 +763,7 @@ static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, f
   }
   if (e == cudaSuccess)
     e = lbrr::launch_mlp_reduce(m->d, m->gpart, nb, grad, adam, lr, bc1, bc2, m->lpart,
-                                loss ? m->dloss : nullptr, m->stream);
+                                loss ? m->dloss : nullptr, m->status, m->stream);
   if (e == cudaSuccess && loss) {
     double h = 0.0;
     e = cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream);
@@ -771,6 +771,8 @@ static int mlp_backward(lb_mlp *m, const void *X, const float *T, long long M, f
     *loss = h / ((double)M * lbrr::kMlpOutUsed);
   }
   if (e != cudaSuccess) return mlp_fail(m, LB_ECUDA, "backward: %s", cudaGetErrorString(e));
+  const int rc = mlp_status(m, m->stream);  // a timed-out pass changed no parameter
+  if (rc != LB_OK) return rc;
   if (adam) ++m->t;
   return LB_OK;
 }

@@ -14,7 +14,7 @@
 // xxyzz, xxyyz, xyyzz, xxyyzz, zero padded to 32.
 #include "lbrr_launch.h"
 #include "lbrr_mlp.h"
-#include "lbrr_mma.cuh"
+#include "lbrr_act.cuh"
 
 namespace lbrr {
 

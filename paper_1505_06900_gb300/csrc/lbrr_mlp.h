@@ -140,7 +140,7 @@ __device__ __forceinline__ void closure_update_cell(const MlpDevice &p, float *_
                                       bound, dead_zone);
 }
 
-size_t mlp_train_smem();
+constexpr int kMlpTrainRows = 128;  // batch rows per tile of the training kernel
 
 // Columns of one trace row of the training kernel (FP32, as computed, before
 // any BF16 rounding): layer-1 and layer-2 activations, outputs, the loss
@@ -149,17 +149,20 @@ size_t mlp_train_smem();
 constexpr int kTraceH1 = 0, kTraceH2 = 64, kTraceY = 128, kTraceDy = 160, kTraceDh2 = 192,
               kTraceDh1 = 256, kMlpTrace = 320;
 
-// Forward + backward of a batch on the warp-level tensor cores (writes the
-// block partial gradients gpart [nblocks][kMlpParams] and losses lpart); with
-// trace also the trace rows [M][kMlpTrace].
+// Forward + backward of a batch on the tcgen05 tensor cores (lbrr_mlp_train.cu):
+// writes the block partial gradients gpart [b][kMlpParams] and loss sums
+// lpart[b] of the min(nblocks, tiles of kMlpTrainRows rows) blocks; with
+// trace also the trace rows [M][kMlpTrace]. *status becomes 1 if a
+// tensor-core wait timed out (the partials are then incomplete).
 cudaError_t launch_mlp_train(const MlpDevice &p, const void *X, const float *T, long long M,
-                             float *gpart, float *lpart, int nblocks, cudaStream_t st,
-                             float *trace = nullptr);
+                             float *gpart, float *lpart, int *status, int nblocks,
+                             cudaStream_t st, float *trace = nullptr);
 // Gradient = sum of the partials; optional Adam step (bias corrections bc1,
 // bc2); loss = sum of the block losses (double, device) when loss_out != null.
+// Nothing is updated while *status (the training kernel's timeout flag) is set.
 cudaError_t launch_mlp_reduce(const MlpDevice &p, const float *gpart, int nparts, float *grad_out,
                               int adam, float lr, float bc1, float bc2, const float *lpart,
-                              double *loss_out, cudaStream_t st);
+                              double *loss_out, const int *status, cudaStream_t st);
 cudaError_t launch_mlp_refresh(const MlpDevice &p, cudaStream_t st);
 
 // Moment field [10][N] of the logical populations (FP32 store only).

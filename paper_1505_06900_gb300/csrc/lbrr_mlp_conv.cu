@@ -61,7 +61,7 @@
 
 #include "lbrr_launch.h"
 #include "lbrr_mlp.h"
-#include "lbrr_mma.cuh"
+#include "lbrr_act.cuh"
 #include "lbrr_tc.cuh"
 
 namespace lbrr {
@@ -92,10 +92,10 @@ constexpr int kEpiWarp0 = 1 + kIssuers;             // first warp of the epilogu
 constexpr int kConvThreads = 32 * (kEpiWarp0 + 4 * kGroups);
 constexpr uint32_t kTmemCols = 512;
 
-constexpr uint32_t kOffW1 = 0;
-constexpr uint32_t kOffW2 = kOffW1 + kMmas1 * kW1Bytes;
-constexpr uint32_t kOffW3 = kOffW2 + kMlpHidden * kMlpHidden * 2;
-constexpr uint32_t kOffA1 = kOffW3 + kMlpOut * kMlpHidden * 2;
+constexpr uint32_t kSmW1 = 0;
+constexpr uint32_t kSmW2 = kSmW1 + kMmas1 * kW1Bytes;
+constexpr uint32_t kSmW3 = kSmW2 + kMlpHidden * kMlpHidden * 2;
+constexpr uint32_t kOffA1 = kSmW3 + kMlpOut * kMlpHidden * 2;
 constexpr uint32_t kOffPop = kOffA1 + kStages * kStageBytes;
 constexpr uint32_t kOffMisc = kOffPop + kGroups * kPopBytes;
 constexpr uint32_t kOffBias = 512;                   // biases, after barriers and counters
@@ -239,18 +239,18 @@ __global__ void __launch_bounds__(kConvThreads, 1)
       w[6] = __bfloat16_as_ushort(hi);
       w[7] = __bfloat16_as_ushort(__float2bfloat16_rn(p.b1[n] - __bfloat162float(hi)));
     }
-    *reinterpret_cast<uint4 *>(smem + kOffW1 + mq * kW1Bytes + h * 1024 + n * 16) =
+    *reinterpret_cast<uint4 *>(smem + kSmW1 + mq * kW1Bytes + h * 1024 + n * 16) =
         make_uint4(w[0] | ((uint32_t)w[1] << 16), w[2] | ((uint32_t)w[3] << 16),
                    w[4] | ((uint32_t)w[5] << 16), w[6] | ((uint32_t)w[7] << 16));
   }
   for (int c = tid; c < kMlpHidden * (kMlpHidden / 8); c += kConvThreads) {
     const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
-    *reinterpret_cast<uint4 *>(smem + kOffW2 + cm_offset(n, 8 * kb, kMlpHidden)) =
+    *reinterpret_cast<uint4 *>(smem + kSmW2 + cm_offset(n, 8 * kb, kMlpHidden)) =
         *reinterpret_cast<const uint4 *>(p.w2 + n * kMlpHidden + 8 * kb);
   }
   for (int c = tid; c < kMlpOut * (kMlpHidden / 8); c += kConvThreads) {
     const int n = c / (kMlpHidden / 8), kb = c - n * (kMlpHidden / 8);
-    *reinterpret_cast<uint4 *>(smem + kOffW3 + cm_offset(n, 8 * kb, kMlpHidden)) =
+    *reinterpret_cast<uint4 *>(smem + kSmW3 + cm_offset(n, 8 * kb, kMlpHidden)) =
         *reinterpret_cast<const uint4 *>(p.w3 + n * kMlpHidden + 8 * kb);
   }
   for (int c = tid; c < 2 * kMlpHidden + kMlpOut + kMlpOutUsed; c += kConvThreads)
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(kConvThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t lim = wait_limit(status);
   const long long ntiles = g.n / kCRows;
-  const uint32_t sw1 = smem_u32(smem + kOffW1), sw2 = smem_u32(smem + kOffW2);
-  const uint32_t sw3 = smem_u32(smem + kOffW3), sa1 = smem_u32(smem + kOffA1);
+  const uint32_t sw1 = smem_u32(smem + kSmW1), sw2 = smem_u32(smem + kSmW2);
+  const uint32_t sw3 = smem_u32(smem + kSmW3), sa1 = smem_u32(smem + kOffA1);
 
   if (warp == 0) {
     // ---------------------------------------------------------- producer

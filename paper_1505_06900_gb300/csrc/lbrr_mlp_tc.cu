@@ -21,7 +21,7 @@
 
 #include "lbrr_launch.h"
 #include "lbrr_mlp.h"
-#include "lbrr_mma.cuh"
+#include "lbrr_act.cuh"
 #include "lbrr_tc.cuh"
 
 namespace lbrr {

@@ -120,11 +120,14 @@ def test_forward_matches_oracle_layer_by_layer(m):
     net.close()
 
 
-@pytest.mark.parametrize("m", [1, 64, 300])
+# m = 19533: more 128-row tiles than a GB300 has SMs, so every block writes
+# its partial gradients and several take two tiles
+@pytest.mark.parametrize("m", [1, 64, 300, 19533])
 def test_gradients_match_oracle_element_by_element(m):
-    """The training kernel (64-row tiles, one per warp group; M = 300 leaves a
-    ragged tile): activations, outputs, loss gradient and back-propagated
-    gradients row by row, then every weight and bias gradient and the loss."""
+    """The tcgen05 training kernel (128-row tiles; M = 1 and 300 leave ragged
+    tiles): activations, outputs, loss gradient and back-propagated gradients
+    row by row, then every weight and bias gradient (the weight gradients from
+    the transposed, MN-major reads of the staged tiles) and the loss."""
     rng = np.random.default_rng(20 + m)
     p = bf16_params(rng)
     X = bf16_inputs(rng, m)
@@ -166,9 +169,11 @@ def test_gradients_match_oracle_element_by_element(m):
     assert np.all(np.abs(DH1 - dh1) <= b_dh1 + 1e-30)
     DH1b = C.bf16_round(DH1)
     # weight gradients: products of the BF16 roundings, FP32 accumulation over
-    # the rows (per tile, per block, then over the blocks)
-    nb = min(-(-m // 64), 152)
-    kacc = (m / 8 + nb + 4) * 2.0 ** -22
+    # the rows: one addition per 16-row MMA step of a block (its tiles in
+    # turn), then the block partials in order
+    tiles = -(-m // 128)
+    nb = min(tiles, 152)  # blocks with rows
+    kacc = (8 * -(-tiles // nb) + nb + 4) * 2.0 ** -22
     for name, L, R in (("W3", DYb, r["A2"]), ("W2", DH2b, r["A1"]), ("W1", DH1b, X)):
         ref = L.T @ R
         bound = kacc * (np.abs(L).T @ np.abs(R))

@@ -84,3 +84,32 @@ def test_network_kernel_timeout_and_recovery():
                                   fresh.populations().cpu().numpy())
     finally:
         net.close()
+
+
+def test_training_kernel_timeout_changes_no_parameter():
+    """The training kernel's waits shortened to one try-wait: a step whose
+    wait expired reports LB_ETIMEOUT and leaves the parameters (and the Adam
+    state) as they were; with the default limit the same network then trains
+    exactly as a fresh copy does."""
+    rng = np.random.default_rng(3)
+    params = (0.05 * rng.standard_normal(B.MLP_PARAMS)).astype(np.float32)
+    X = torch.from_numpy(rng.standard_normal((1000, 288)).astype(np.float32)).cuda()
+    X[:, 270:] = 0
+    X = X.to(torch.bfloat16)
+    T = torch.from_numpy(rng.standard_normal((1000, 32)).astype(np.float32)).cuda()
+    net, fresh = B.MLP(params), B.MLP(params)
+    try:
+        net.set_wait_limit(1)
+        timed_out = _reported(lambda: net.train_step(X, T, 1e-3))
+        print("training kernel with one try-wait: timeout reported =", timed_out)
+        if timed_out:
+            assert np.array_equal(net.get_params(), params)
+        net.set_wait_limit(0)
+        if not timed_out:
+            fresh.train_step(X, T, 1e-3)
+        for _ in range(3):
+            assert net.train_step(X, T, 1e-3) == fresh.train_step(X, T, 1e-3)
+        assert np.array_equal(net.get_params(), fresh.get_params())
+    finally:
+        net.close()
+        fresh.close()
