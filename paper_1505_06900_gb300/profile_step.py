@@ -2,6 +2,7 @@
 
     python -m paper_1505_06900_gb300.profile_step [--n 256] [--storage f32|f16|bf16]
                                                   [--lattice 27|19|9] [--steps 6]
+                                                  [--closure | --train BATCH]
 
 Initialises a Taylor-Green vortex on an n^3 (D3Q27, D3Q19) or n^2 (D2Q9) periodic
 grid, runs `steps` updates through the C ABI and prints the elapsed time. At
@@ -30,8 +31,28 @@ def main():
     ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--closure", action="store_true",
                     help="run the learned-closure update (D3Q27, FP32) with small random weights")
+    ap.add_argument("--train", type=int, default=0, metavar="BATCH",
+                    help="instead: `steps` Adam steps of the closure network on a random "
+                         "batch of BATCH rows")
     args = ap.parse_args()
     build_mod.build()
+    if args.train:
+        rng = np.random.default_rng(0)
+        X = torch.from_numpy(rng.standard_normal((args.train, 288)).astype(np.float32)).cuda()
+        X[:, 270:] = 0
+        X = X.to(torch.bfloat16)
+        T = torch.from_numpy(rng.standard_normal((args.train, 32)).astype(np.float32)).cuda()
+        net = B.MLP((0.05 * rng.standard_normal(B.MLP_PARAMS)).astype(np.float32))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            net.train_step(X, T, 1e-3, want_loss=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        print(f"closure network, batch {args.train}: {args.steps} Adam steps in {dt * 1e3:.2f} ms "
+              f"(loss {net.train_step(X, T, 1e-3):.6f})")
+        net.close()
+        return
     storage = {"f32": B.STORE_F32, "f16": B.STORE_F16, "bf16": B.STORE_BF16}[args.storage]
     n = args.n
     if args.lattice != 9:
