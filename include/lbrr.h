@@ -271,7 +271,10 @@ LB_API int lb_mlp_forward_trace(lb_mlp *mlp, const void *X, long long M, float *
 LB_API int lb_mlp_gradients_trace(lb_mlp *mlp, const void *X, const float *T, long long M,
                                   float *grad, double *loss, float *trace);
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the
- * batch; *loss (host, may be NULL) is the loss before the step. */
+ * batch; *loss (host, may be NULL) is the loss before the step. With loss
+ * NULL the call does not synchronise: if a tensor-core wait of the pass timed
+ * out, no parameter changes (nor in later steps) and the next synchronising
+ * call on this network returns LB_ETIMEOUT. */
 LB_API int lb_mlp_train_step(lb_mlp *mlp, const void *X, const float *T, long long M, float lr,
                              double *loss);
 /* Features of every cell of a D3Q27 FP32 RR context into X [N][288] (device). */

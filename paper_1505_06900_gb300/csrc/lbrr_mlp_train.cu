@@ -223,13 +223,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     const long long row = tile * kRows + r;
     const bool valid = row < M;
     float *trow = TRACE && valid ? trace + row * kMlpTrace : nullptr;
-    // ---- input rows (zero past M)
-#pragma unroll 3
+    // ---- input rows: every 16-byte chunk of the thread's half row in flight
+    // at once (cp.async), zeros past M
+#pragma unroll
     for (int kb = half * (kMlpIn / 16); kb < (half + 1) * (kMlpIn / 16); ++kb) {
-      const uint4 q = valid ? *reinterpret_cast<const uint4 *>(X + row * kMlpIn + 8 * kb)
-                            : make_uint4(0u, 0u, 0u, 0u);
-      *reinterpret_cast<uint4 *>(smem + kSmX + cm_offset(r, 8 * kb, kMlpIn)) = q;
+      unsigned char *dst = smem + kSmX + cm_offset(r, 8 * kb, kMlpIn);
+      if (valid)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)),
+                     "l"(X + row * kMlpIn + 8 * kb)
+                     : "memory");
+      else
+        *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
+    cp_async_wait_all();
     handoff();
     // ---- layer 1
     if (tid == 0) {
