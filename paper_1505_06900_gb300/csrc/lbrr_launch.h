@@ -33,6 +33,12 @@ cudaError_t launch_step_walls(int q, int storage, int model, void *f, const Grid
 cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid &g, float om1,
                               int parity, int *status, cudaStream_t st, bool &launched);
 
+// The even (parity 0) update of a 16-bit store with direct paired accesses
+// (lbrr_pair16.cu); usable when pair16_even_supported(g) (nx a multiple of 64).
+bool pair16_even_supported(const Grid &g);
+cudaError_t launch_step_pair16_even(int q, int storage, int model, void *f, const Grid &g,
+                                    float om1, cudaStream_t st);
+
 // The shared-memory tiled variant of launch_step for 16-bit stores
 // (lbrr_step16.cu); usable when tiled16_supported(g) (nx a multiple of 128).
 bool tiled16_supported(const Grid &g);

@@ -20,6 +20,33 @@
 #include "lbrr_device.cuh"
 
 namespace lbrr {
+
+// FP16 / BF16 values of the 16-bit stores, singly and as packed pairs.
+template <int S>
+struct Half;
+template <>
+struct Half<1> {
+  using T2 = __half2;
+  __device__ __forceinline__ static float to_f(__half v) { return __half2float(v); }
+  __device__ __forceinline__ static __half from_f(float v) { return __float2half_rn(v); }
+  __device__ __forceinline__ static float2 to_f2(__half2 v) { return __half22float2(v); }
+  __device__ __forceinline__ static __half2 from_f2(float2 v) { return __float22half2_rn(v); }
+};
+template <>
+struct Half<2> {
+  using T2 = __nv_bfloat162;
+  __device__ __forceinline__ static float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+  __device__ __forceinline__ static __nv_bfloat16 from_f(float v) {
+    return __float2bfloat16_rn(v);
+  }
+  __device__ __forceinline__ static float2 to_f2(__nv_bfloat162 v) {
+    return __bfloat1622float2(v);
+  }
+  __device__ __forceinline__ static __nv_bfloat162 from_f2(float2 v) {
+    return __float22bfloat162_rn(v);
+  }
+};
+
 namespace pair {
 
 using V = float2;

@@ -32,31 +32,6 @@ constexpr int kTileX = 128;                    // shortest row segment (cells pe
 constexpr int kHalo = 8;                       // one 16-byte chunk of halo per side
 constexpr int kChunk = 8;                      // 16-bit values per 16-byte chunk
 
-template <int S>
-struct Half;
-template <>
-struct Half<1> {
-  using T2 = __half2;
-  __device__ __forceinline__ static float to_f(__half v) { return __half2float(v); }
-  __device__ __forceinline__ static __half from_f(float v) { return __float2half_rn(v); }
-  __device__ __forceinline__ static float2 to_f2(__half2 v) { return __half22float2(v); }
-  __device__ __forceinline__ static __half2 from_f2(float2 v) { return __float22half2_rn(v); }
-};
-template <>
-struct Half<2> {
-  using T2 = __nv_bfloat162;
-  __device__ __forceinline__ static float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-  __device__ __forceinline__ static __nv_bfloat16 from_f(float v) {
-    return __float2bfloat16_rn(v);
-  }
-  __device__ __forceinline__ static float2 to_f2(__nv_bfloat162 v) {
-    return __bfloat1622float2(v);
-  }
-  __device__ __forceinline__ static __nv_bfloat162 from_f2(float2 v) {
-    return __float22bfloat162_rn(v);
-  }
-};
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");

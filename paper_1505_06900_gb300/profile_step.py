@@ -2,6 +2,7 @@
 
     python -m paper_1505_06900_gb300.profile_step [--n 256] [--storage f32|f16|bf16]
                                                   [--lattice 27|19|9] [--steps 6]
+                                                  [--collision rr|reg2|bgk]
                                                   [--closure | --train BATCH]
 
 Initialises a Taylor-Green vortex on an n^3 (D3Q27, D3Q19) or n^2 (D2Q9) periodic
@@ -29,6 +30,7 @@ def main():
     ap.add_argument("--lattice", type=int, default=27, choices=[9, 19, 27])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--collision", default="rr", choices=["rr", "reg2", "bgk"])
     ap.add_argument("--closure", action="store_true",
                     help="run the learned-closure update (D3Q27, FP32) with small random weights")
     ap.add_argument("--train", type=int, default=0, metavar="BATCH",
@@ -64,7 +66,8 @@ def main():
         rho, u = W.taylor_green_2d(n, 0.05)
         tau = W.taylor_green_2d_tau(n, 0.05)
     net = None
-    with B.Solver(args.lattice, shape, tau, storage=storage) as s:
+    collision = {"rr": B.COLLIDE_RR, "reg2": B.COLLIDE_REG2, "bgk": B.COLLIDE_BGK}[args.collision]
+    with B.Solver(args.lattice, shape, tau, storage=storage, collision=collision) as s:
         s.init_fields(torch.from_numpy(rho.astype(np.float32)).cuda(),
                       torch.from_numpy(u.astype(np.float32)).cuda())
         if args.closure:
@@ -82,7 +85,8 @@ def main():
     if net is not None:
         net.close()
     cells = int(np.prod(shape))
-    print(f"lattice D{2 if args.lattice == 9 else 3}Q{args.lattice} {shape} {args.storage}: "
+    print(f"lattice D{2 if args.lattice == 9 else 3}Q{args.lattice} {shape} {args.storage} "
+          f"{args.collision}: "
           f"{args.steps} steps in {dt * 1e3:.2f} ms ({cells * args.steps / dt / 1e9:.2f} GLUPS), "
           f"mass {d[0]:.6f}")
 

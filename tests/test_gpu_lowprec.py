@@ -60,20 +60,24 @@ def raw_store(g: np.ndarray, storage: int, parity: int, c: np.ndarray) -> "torch
 @pytest.mark.parametrize("storage", [B.STORE_F16, B.STORE_BF16])
 @pytest.mark.parametrize("parity", [0, 1])
 @pytest.mark.parametrize("collision", [B.COLLIDE_RR, B.COLLIDE_REG2, B.COLLIDE_BGK])
-# The 16-bit kernels by row length nx: row segments of 256 cells for
+# The 16-bit kernels by row length nx. Even update (parity 0): two cells per
+# thread with direct accesses for nx % 64 == 0 (blocks of 256 cells: one per
+# row, several, a partial last block (192, 320), a row of one warp (64)).
+# Odd update, and the even one for other nx: row segments of 256 cells for
 # nx % 256 == 0 and of 128 cells for other nx % 128 == 0 (one segment per row
 # and several, including rows longer than the whole-row kernel takes); whole
 # rows for other nx % 16 == 0 with 64 <= nx <= 1024 (D3Q27) / 2048 (D2Q9),
 # including a partial second warp (nx = 80) and a single row; one thread per
-# cell otherwise; the same kernels serve D3Q19.
+# cell otherwise. The same kernels serve D3Q19.
 @pytest.mark.parametrize("lattice,shape", [
     (O.D2Q9, (256, 3, 1)), (O.D2Q9, (768, 3, 1)), (O.D2Q9, (128, 4, 1)),
-    (O.D2Q9, (2176, 2, 1)), (O.D2Q9, (208, 4, 1)), (O.D2Q9, (96, 1, 1)),
-    (O.D2Q9, (260, 5, 1)),
+    (O.D2Q9, (2176, 2, 1)), (O.D2Q9, (192, 3, 1)), (O.D2Q9, (64, 1, 1)),
+    (O.D2Q9, (208, 4, 1)), (O.D2Q9, (96, 1, 1)), (O.D2Q9, (260, 5, 1)),
     (O.D3Q27, (256, 3, 4)), (O.D3Q27, (512, 2, 3)), (O.D3Q27, (1152, 3, 2)),
+    (O.D3Q27, (64, 3, 2)), (O.D3Q27, (320, 2, 3)),
     (O.D3Q27, (144, 3, 3)), (O.D3Q27, (80, 3, 2)), (O.D3Q27, (140, 5, 4)),
-    (O.D3Q19, (256, 3, 4)), (O.D3Q19, (384, 2, 3)), (O.D3Q19, (144, 3, 3)),
-    (O.D3Q19, (80, 3, 2)), (O.D3Q19, (140, 5, 4))])
+    (O.D3Q19, (256, 3, 4)), (O.D3Q19, (384, 2, 3)), (O.D3Q19, (192, 3, 2)),
+    (O.D3Q19, (144, 3, 3)), (O.D3Q19, (80, 3, 2)), (O.D3Q19, (140, 5, 4))])
 def test_one_update_is_correctly_rounded(storage, parity, collision, lattice, shape):
     """Every 16-bit kernel (the store is written at either parity from the host)."""
     variant = {B.COLLIDE_RR: O.RR, B.COLLIDE_REG2: O.REG2, B.COLLIDE_BGK: O.BGK}[collision]
