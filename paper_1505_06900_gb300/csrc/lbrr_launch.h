@@ -21,6 +21,11 @@ constexpr int kRedValues = 5;      // partial sums per block (mass, momentum x3,
 cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
                         int parity, int *status, cudaStream_t st);
 
+// The one-thread-per-cell kernel of launch_step (lbrr_step.cu), for any grid
+// without walls and any storage.
+cudaError_t launch_step_cell(int q, int storage, int model, void *f, const Grid &g, float om1,
+                             int parity, cudaStream_t st);
+
 // The update of a grid with no-slip walls (g.walls != 0; lbrr_walls.cu),
 // any storage; launch_step dispatches to it.
 cudaError_t launch_step_walls(int q, int storage, int model, void *f, const Grid &g, float om1,
@@ -39,11 +44,12 @@ bool pair16_even_supported(const Grid &g);
 cudaError_t launch_step_pair16_even(int q, int storage, int model, void *f, const Grid &g,
                                     float om1, cudaStream_t st);
 
-// The shared-memory tiled variant of launch_step for 16-bit stores
-// (lbrr_step16.cu); usable when tiled16_supported(g) (nx a multiple of 128).
+// The odd (parity 1) update of a 16-bit store through shared-memory row
+// segments (lbrr_step16.cu); usable when tiled16_supported(g) (nx a multiple
+// of 128).
 bool tiled16_supported(const Grid &g);
-cudaError_t launch_step_tiled16(int q, int storage, int model, void *f, const Grid &g, float om1,
-                                int parity, cudaStream_t st);
+cudaError_t launch_step_tiled16_odd(int q, int storage, int model, void *f, const Grid &g,
+                                    float om1, cudaStream_t st);
 
 // f = f0 + f1 (mode 1) or f0 (mode 0) from device fields rho [N], u [D][N].
 cudaError_t launch_init(int q, int storage, int model, void *f, const Grid &g, const float *rho,

@@ -108,20 +108,8 @@ static cudaError_t step_s(int storage, int model, void *f, const Grid &g, float 
   }
 }
 
-cudaError_t launch_step(int q, int storage, int model, void *f, const Grid &g, float om1,
-                        int parity, int *status, cudaStream_t st) {
-  if (g.walls) return launch_step_walls(q, storage, model, f, g, om1, parity, st);
-  // 16-bit stores: the even update with direct paired accesses where nx
-  // allows; otherwise, and for the odd update, row segments of 128 or 256
-  // cells where nx allows, else whole rows, else one thread per cell
-  if (storage != 0) {
-    if (parity == 0 && pair16_even_supported(g))
-      return launch_step_pair16_even(q, storage, model, f, g, om1, st);
-    if (tiled16_supported(g)) return launch_step_tiled16(q, storage, model, f, g, om1, parity, st);
-    bool launched = false;
-    cudaError_t e = launch_step_row16(q, storage, model, f, g, om1, parity, status, st, launched);
-    if (e != cudaSuccess || launched) return e;
-  }
+cudaError_t launch_step_cell(int q, int storage, int model, void *f, const Grid &g, float om1,
+                             int parity, cudaStream_t st) {
   if (q == 9) return step_s<9>(storage, model, f, g, om1, parity, st);
   if (q == 19) return step_s<19>(storage, model, f, g, om1, parity, st);
   return step_s<27>(storage, model, f, g, om1, parity, st);

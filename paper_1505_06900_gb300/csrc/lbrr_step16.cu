@@ -20,7 +20,8 @@
 // x - xi_i and writes slot i of x + xi_i. Slot s is therefore read from and
 // written to the same row (y + cy_s, z + cz_s) in an odd update. A location
 // outside the block's cells may be read as halo while its owner rewrites it;
-// the value is never used. Requires nx to be a multiple of TX.
+// the value is never used. Requires nx to be a multiple of TX. The library
+// launches the odd form only (see tiled_tx below).
 #include <algorithm>
 
 #include "lbrr_launch.h"
@@ -454,45 +455,43 @@ cudaError_t launch_step_row16(int q, int storage, int model, void *f, const Grid
                       : row_m<27, 2>(model, f, g, om1, parity, status, st, launched);
 }
 
+// Only the odd form is launched: every row length this kernel takes
+// (nx % 128 == 0) has its even update in the direct kernel of lbrr_pair16.cu.
 template <int Q, int S, int MODEL, int TX>
-static cudaError_t tiled_tx(void *f, const Grid &g, float om1, int parity, cudaStream_t st) {
+static cudaError_t tiled_tx(void *f, const Grid &g, float om1, cudaStream_t st) {
   using T = typename Storage<S>::T;
   const dim3 grid(g.nx / TX, g.ny, g.nz);
-  if (parity == 0)
-    rr_step_tiled16_kernel<Q, S, MODEL, 0, TX><<<grid, TX / 2, 0, st>>>(static_cast<T *>(f), g, om1);
-  else
-    rr_step_tiled16_kernel<Q, S, MODEL, 1, TX><<<grid, TX / 2, 0, st>>>(static_cast<T *>(f), g, om1);
+  rr_step_tiled16_kernel<Q, S, MODEL, 1, TX><<<grid, TX / 2, 0, st>>>(static_cast<T *>(f), g, om1);
   return cudaGetLastError();
 }
 
 template <int Q, int S, int MODEL>
-static cudaError_t tiled_t(void *f, const Grid &g, float om1, int parity, cudaStream_t st) {
-  if (g.nx % 256 == 0) return tiled_tx<Q, S, MODEL, 256>(f, g, om1, parity, st);
-  return tiled_tx<Q, S, MODEL, 128>(f, g, om1, parity, st);
+static cudaError_t tiled_t(void *f, const Grid &g, float om1, cudaStream_t st) {
+  if (g.nx % 256 == 0) return tiled_tx<Q, S, MODEL, 256>(f, g, om1, st);
+  return tiled_tx<Q, S, MODEL, 128>(f, g, om1, st);
 }
 
 bool tiled16_supported(const Grid &g) { return g.nx % kTileX == 0; }
 
 template <int Q, int S>
-static cudaError_t tiled_m(int model, void *f, const Grid &g, float om1, int parity,
-                           cudaStream_t st) {
+static cudaError_t tiled_m(int model, void *f, const Grid &g, float om1, cudaStream_t st) {
   switch (model) {
-    case 0: return tiled_t<Q, S, 0>(f, g, om1, parity, st);
-    case 1: return tiled_t<Q, S, 1>(f, g, om1, parity, st);
-    default: return tiled_t<Q, S, 2>(f, g, om1, parity, st);
+    case 0: return tiled_t<Q, S, 0>(f, g, om1, st);
+    case 1: return tiled_t<Q, S, 1>(f, g, om1, st);
+    default: return tiled_t<Q, S, 2>(f, g, om1, st);
   }
 }
 
-cudaError_t launch_step_tiled16(int q, int storage, int model, void *f, const Grid &g, float om1,
-                                int parity, cudaStream_t st) {
+cudaError_t launch_step_tiled16_odd(int q, int storage, int model, void *f, const Grid &g,
+                                    float om1, cudaStream_t st) {
   if (q == 9)
-    return storage == 1 ? tiled_m<9, 1>(model, f, g, om1, parity, st)
-                        : tiled_m<9, 2>(model, f, g, om1, parity, st);
+    return storage == 1 ? tiled_m<9, 1>(model, f, g, om1, st)
+                        : tiled_m<9, 2>(model, f, g, om1, st);
   if (q == 19)
-    return storage == 1 ? tiled_m<19, 1>(model, f, g, om1, parity, st)
-                        : tiled_m<19, 2>(model, f, g, om1, parity, st);
-  return storage == 1 ? tiled_m<27, 1>(model, f, g, om1, parity, st)
-                      : tiled_m<27, 2>(model, f, g, om1, parity, st);
+    return storage == 1 ? tiled_m<19, 1>(model, f, g, om1, st)
+                        : tiled_m<19, 2>(model, f, g, om1, st);
+  return storage == 1 ? tiled_m<27, 1>(model, f, g, om1, st)
+                      : tiled_m<27, 2>(model, f, g, om1, st);
 }
 
 }  // namespace lbrr
